@@ -1,0 +1,331 @@
+"""Benchmark: exact products of 2^20-bit integers per second on GB300.
+
+Workload (one "step"): a batch of P balanced products of two 2^20-bit
+operands (32768 uint32 limbs each, limbs uniform from a seed) through the
+whole Toom-Cook path (evaluation, recursive pointwise products, schoolbook
+base case, interpolation, recomposition) in one library call.  P = 608 per
+GPU (4 x 152 SMs), so the operands alone (152 MB) exceed the 129 MB L2 and
+no L2 flush is needed between steps.
+
+Prints one JSON line (rank 0).  `value` is whole-job products per second
+(Mults/s); `e2e` is the same metric through the host-buffer entry point
+with the host<->device copies inside the timed region; `roofline` describes
+the dominant kernel; `cpu_baseline` is the CPU oracle (plain schoolbook) on
+a bounded sample on this machine's host cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import signal
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+LIMBS = 32768            # 2^20 bits
+PER_GPU = 608            # 4 x 152 SMs
+SM_COUNT = 152
+IMAD_PER_CLK_SM = 64     # 32-bit integer multiply(-add) results per clock per SM
+IMAD_PER_LIMB_PRODUCT = 2  # low and high halves of a 32 x 32 -> 64-bit product
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="tc", choices=["tc", "reference"])
+    p.add_argument("--limbs", type=int, default=LIMBS)
+    p.add_argument("--batch", type=int, default=PER_GPU)
+    p.add_argument("--plan", default="auto", help="comma-separated B per level, or auto")
+    p.add_argument("--no-sweep", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    return p.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ----------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.file, stderr=subprocess.DEVNULL, start_new_session=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        try:
+            os.killpg(self.proc.pid, signal.SIGTERM)
+        except OSError:
+            pass
+        self.proc.wait(timeout=5)
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r.split(",") for r in self.file.read().strip().splitlines() if r.strip()]
+        os.unlink(self.file.name)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- CPU oracle leg
+
+def cpu_oracle_rate(limbs: int, seconds_budget: float = 20.0):
+    """Products/s of the oracle's C schoolbook on this host's cores (bounded sample)."""
+    from concurrent.futures import ThreadPoolExecutor
+    from oracle import native
+    from paper_1602_02740_gb300 import inputs
+    cores = os.cpu_count() or 1
+    a = inputs.uniform(limbs, 101)
+    b = inputs.uniform(limbs, 102)
+    t0 = time.perf_counter()
+    native.schoolbook(a, b)                      # one product: calibrates the sample size
+    one = time.perf_counter() - t0
+    per_thread = max(1, int(seconds_budget / max(one, 1e-6) / cores))
+    n = per_thread * cores
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=cores) as ex:
+        list(ex.map(lambda _: native.schoolbook(a, b), range(n)))
+    wall = time.perf_counter() - t0
+    return {"value": n / wall, "unit": "mults/s", "cores": cores, "kind": "oracle",
+            "sample": f"{n} products of {limbs}x{limbs} limbs by the plain C schoolbook, "
+                      f"{cores} threads, {wall:.1f} s wall"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    limbs = args.limbs
+    rates = []
+    cpu = None
+    for i in range(args.warmup + args.steps):
+        r = cpu_oracle_rate(limbs, seconds_budget=4.0 if i >= args.warmup else 1.0)
+        if i >= args.warmup:
+            rates.append(r["value"])
+            cpu = r
+    value = statistics.median(rates)
+    cpu["value"] = value
+    line = {"impl": "reference", "metric": "exact 2^20-bit products per second (Mults/s)",
+            "value": value, "unit": "mults/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": f"balanced {limbs * 32}-bit products, uniform limbs",
+                       "limbs": limbs},
+            "cpu_baseline": cpu,
+            "e2e": {"value": value, "unit": "mults/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------- GPU leg
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    from paper_1602_02740_gb300 import inputs, tc
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    L, P = args.limbs, args.batch
+    ctx = tc.tc_create(local)
+    plan = None if args.plan == "auto" else [int(x) for x in args.plan.split(",")]
+    used_plan = plan or tc.tc_plan_for(ctx, L)
+
+    # seeded operands (host generation, one upload)
+    A = np.empty((P, L), dtype=np.uint32)
+    B = np.empty((P, L), dtype=np.uint32)
+    for k in range(P):
+        A[k] = inputs.uniform(L, 1_000_000 * rank + 2 * k)
+        B[k] = inputs.uniform(L, 1_000_000 * rank + 2 * k + 1)
+    dA, dB = tc.to_device(A), tc.to_device(B)
+    dO = torch.empty((P, 2 * L), dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    for _ in range(max(3, args.warmup)):
+        tc.tc_mul_uniform(ctx, dA, dB, dO, plan=used_plan)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    tc.tc_profile_enable(ctx, True)
+    barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        tc.tc_mul_uniform(ctx, dA, dB, dO, plan=used_plan)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms_total = ev0.elapsed_time(ev1)
+    phases = tc.tc_profile_read(ctx)
+    tc.tc_profile_enable(ctx, False)
+    clk = clocks.stop()
+    if dist is not None:
+        t = torch.tensor([ms_total], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    value = world * P / (ms_step / 1e3)
+    launches = sum(p["launches"] for p in phases)
+
+    # ---- end to end through the host-buffer entry point (pinned memory) ----
+    hA = torch.from_numpy(A.view(np.int32)).pin_memory()
+    hB = torch.from_numpy(B.view(np.int32)).pin_memory()
+    hO = torch.empty((P, 2 * L), dtype=torch.int32).pin_memory()
+    tc.tc_mul_uniform_host(ctx, hA, hB, hO, plan=used_plan)
+    e2e_steps = max(3, min(args.steps, 10))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        tc.tc_mul_uniform_host(ctx, hA, hB, hO, plan=used_plan)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * P / e2e_s, "unit": "mults/s",
+           "h2d_bytes_per_step": 2 * P * L * 4, "d2h_bytes_per_step": P * 2 * L * 4}
+
+    # ---- B sweep (top-level B in {2,3,4,8,16}, best lower levels of a few) ----
+    sweep = None
+    if not args.no_sweep:
+        cands = {2: [[2, 16, 8, 3], [2, 8, 8, 4]], 3: [[3, 16, 4, 3], [3, 8, 8, 3]],
+                 4: [[4, 16, 4, 3], [4, 8, 8, 3]], 8: [[8, 8, 8], [8, 16, 4]],
+                 16: [[16, 8, 3], [16, 8, 4], [16, 16]]}
+        sweep = {}
+        for Btop, plans in cands.items():
+            best = None
+            for pl in plans:
+                try:
+                    tc.tc_mul_uniform(ctx, dA, dB, dO, plan=pl)
+                except tc.TCError:
+                    continue
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(3):
+                    tc.tc_mul_uniform(ctx, dA, dB, dO, plan=pl)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / 3
+                if best is None or ms < best[0]:
+                    best = (ms, pl)
+            if best:
+                sweep[str(Btop)] = {"plan": best[1], "mults_per_s": P / (best[0] / 1e3),
+                                    "ns_per_product": best[0] * 1e6 / P}
+
+    # ---- roofline of the dominant phase ----
+    pk, pk_src = peaks()
+    top = max(phases, key=lambda p: p["ms"])
+    avg_ms = top["ms"] / top["launches"]
+    if top["kind"] == "base_case":
+        mhz = pk.get("sm_max_mhz", 2070.0)
+        peak = SM_COUNT * IMAD_PER_CLK_SM / IMAD_PER_LIMB_PRODUCT * mhz * 1e6 / 1e12
+        achieved = top["limb_products"] / top["launches"] / (avg_ms / 1e3) / 1e12
+        roof = {"kernel": "leaf_kernel", "bound": "alu", "achieved": achieved, "peak": peak,
+                "unit": "T limb-products/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": f"derived: {SM_COUNT} SMs x {IMAD_PER_CLK_SM} IMAD/clk / "
+                               f"{IMAD_PER_LIMB_PRODUCT} x {mhz:.0f} MHz"}
+    else:
+        peak = pk["hbm_gbs"]
+        achieved = top["bytes"] / top["launches"] / (avg_ms / 1e3) / 1e9
+        name = "interp_kernel" if top["kind"] == "interpolate" else "eval_kernel"
+        roof = {"kernel": name, "level": top["level"], "bound": "hbm", "achieved": achieved,
+                "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": f"{pk_src} hbm_gbs (MEASURED_PEAKS.json)"}
+    phase_summary = [{"kind": p["kind"], "level": p["level"],
+                      "ms_per_step": p["ms"] / args.steps,
+                      "share": p["ms"] / sum(q["ms"] for q in phases)} for p in phases]
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_oracle_rate(L)
+
+    if rank == 0:
+        line = {
+            "metric": "exact 2^20-bit products per second (Mults/s)",
+            "value": value, "unit": "mults/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "ns_per_product": ms_step * 1e6 / P,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic",
+            "config": {"workload": f"batch of {P} balanced {L * 32}-bit products per GPU, "
+                                   "uniform random limbs (B sweep at 2^20 bits)",
+                       "limbs": L, "batch_per_gpu": P, "plan": used_plan,
+                       "l2": "operands (152 MB) exceed the 129 MB L2; no flush"},
+            "roofline": roof, "phases": phase_summary, "sweep": sweep,
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

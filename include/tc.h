@@ -1,0 +1,238 @@
+/*
+ * tc.h - exact B-way Toom-Cook multiplication of large unsigned integers on
+ * an NVIDIA GB300 (sm_103a).  C ABI; every entry point is extern "C".
+ *
+ * The operation is the product w = u v of two unsigned integers (Section 1 of
+ * Kronenburg, "Toom-Cook Multiplication: Some Theoretical and Practical
+ * Aspects", arXiv:1602.02740: u = U(2^b), v = V(2^b), w = W(2^b)), computed by
+ * B-way Toom-Cook: split into B blocks, evaluate at the 2B-1 points 0 and
+ * +-2^j (Section 6), multiply pointwise (recursively), interpolate with the
+ * even-odd method (Section 4) and Newton's divided differences with exact
+ * divisions (Section 3, Theorems 3.2 and 3.3), and recompose.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - An integer is a little-endian array of uint32 limbs: limb i holds bits
+ *   [32 i, 32 i + 32).  Lengths are in limbs.
+ * - "Device pointer" means memory the CUDA device can read (cudaMalloc,
+ *   managed, or a torch CUDA tensor's storage) on the context's device.
+ *   "Host pointer" means ordinary or pinned host memory.
+ * - Output buffers must not overlap input buffers.
+ * - `stream` is a cudaStream_t passed as void*; NULL means the legacy default
+ *   stream.  Calls are asynchronous with respect to the host unless stated;
+ *   results are valid once the stream has completed.
+ * - The caller owns every buffer it passes.  The context owns its scratch
+ *   memory (allocated with cudaMalloc, never above the context's budget).
+ * - Errors are returned as tc_status; nothing aborts, traps or throws.
+ *   Argument errors are detected on the host before any launch.
+ * - Calls that share one context must not run concurrently (they share its
+ *   scratch); use one context per concurrent stream.  The serving calls are
+ *   the exception: they are thread-safe.
+ */
+#ifndef TC_H
+#define TC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tc_ctx tc_ctx;
+
+typedef enum {
+    TC_OK = 0,
+    TC_EINVAL = -1,     /* bad argument (null pointer, size, plan) */
+    TC_ENOMEM = -2,     /* scratch would exceed the context budget, or cudaMalloc failed */
+    TC_EBUSY = -3,      /* serving: not admitted now (budget or slots full) */
+    TC_ETIMEOUT = -4,   /* a bounded wait gave up */
+    TC_EDEVICE = -5,    /* a CUDA call failed; see tc_last_cuda_error */
+    TC_EPENDING = 1     /* serving: request still running */
+} tc_status;
+
+#define TC_MAX_LEVELS 8
+
+/*
+ * Recursion plan.  levels = number of Toom levels above the schoolbook base
+ * case (0 = plain schoolbook); B[l] is the number of blocks at level l
+ * (2 <= B[l] <= 32).  Block size at a level of operand length s is
+ * b = ceil(s / B); each evaluation value has e = b + ceil((n(n-1)+1)/32)
+ * limbs (n = B-1), which is the operand length of the next level.
+ * Passing NULL for a `const tc_opts*` lets the library choose the plan
+ * (autotuned table if loaded, else a built-in rule).
+ */
+typedef struct {
+    int levels;
+    int B[TC_MAX_LEVELS];
+} tc_opts;
+
+/* Create a context on CUDA device `device` whose scratch never exceeds
+ * `hbm_budget_bytes` (0 = 3/4 of the device's free memory).
+ * `tune_table_path` (nullable) names a plan table written by the autotuner:
+ * text lines "<max_limbs> <levels> <B0> <B1> ...", ascending max_limbs.
+ * On success *ctx is set and TC_OK returned. */
+tc_status tc_create(tc_ctx **ctx, int device, size_t hbm_budget_bytes,
+                    const char *tune_table_path);
+
+/* Free the context and its scratch (synchronises the device first). */
+void tc_destroy(tc_ctx *ctx);
+
+/* The plan the library would use for balanced operands of `limbs` limbs. */
+tc_status tc_plan_for(tc_ctx *ctx, size_t limbs, tc_opts *plan_out);
+
+/* Scratch bytes a balanced batch of `count` products of `limbs` limbs needs
+ * under `opts` (NULL = the library's plan). */
+tc_status tc_scratch_bytes(tc_ctx *ctx, size_t count, size_t limbs, const tc_opts *opts,
+                           size_t *bytes_out);
+
+/*
+ * out[0 .. na+nb) = a[0 .. na) * b[0 .. nb)   (device pointers).
+ * Exactly na+nb limbs are written (leading zeros kept).  na == 0 or nb == 0
+ * zero-fills out.  a == b with na == nb selects the squaring path.
+ * Unbalanced operands: the shorter operand is zero-padded when the ratio is
+ * below 2; otherwise the longer one is cut into pieces of the shorter's
+ * length, the pieces are multiplied as one balanced batch, and the partial
+ * products are added at their offsets.
+ */
+tc_status tc_mul(tc_ctx *ctx, const uint32_t *a, size_t na, const uint32_t *b, size_t nb,
+                 uint32_t *out, const tc_opts *opts, void *stream);
+
+/* out[0 .. 2 na) = a^2 (device pointers). */
+tc_status tc_sqr(tc_ctx *ctx, const uint32_t *a, size_t na, uint32_t *out,
+                 const tc_opts *opts, void *stream);
+
+/*
+ * `count` independent products in one call.  A, Bv and OUT are device limb
+ * buffers; a_off/a_len, b_off/b_len and out_off are HOST int64 arrays of
+ * limb offsets and lengths.  Product k reads A[a_off[k] .. +a_len[k]) and
+ * Bv[b_off[k] .. +b_len[k]) and writes OUT[out_off[k] .. +a_len[k]+b_len[k]).
+ * Products are grouped into size classes; each class runs level by level
+ * (breadth first) with every product of the class in the same launches.
+ */
+tc_status tc_mul_batch(tc_ctx *ctx, size_t count,
+                       const uint32_t *A, const int64_t *a_off, const int64_t *a_len,
+                       const uint32_t *Bv, const int64_t *b_off, const int64_t *b_len,
+                       uint32_t *OUT, const int64_t *out_off,
+                       const tc_opts *opts, void *stream);
+
+/*
+ * Uniform batch: `count` balanced products of `limbs` x `limbs` limbs stored
+ * as rows.  A row k is A[k * lda .. k * lda + limbs), likewise B; the result
+ * row is OUT[k * ldo .. k * ldo + 2 limbs).  Device pointers.
+ */
+tc_status tc_mul_uniform(tc_ctx *ctx, size_t count, size_t limbs,
+                         const uint32_t *A, size_t lda, const uint32_t *Bv, size_t ldb,
+                         uint32_t *OUT, size_t ldo, const tc_opts *opts, void *stream);
+
+/*
+ * Same as tc_mul_uniform but A, Bv and OUT are HOST pointers (pinned memory
+ * gives full copy speed).  Copies in, multiplies, copies out and waits for
+ * the stream before returning.
+ */
+tc_status tc_mul_uniform_host(tc_ctx *ctx, size_t count, size_t limbs,
+                              const uint32_t *A, const uint32_t *Bv, uint32_t *OUT,
+                              const tc_opts *opts, void *stream);
+
+/* ---------------------------------------------------------------------
+ * The steps of one Toom level, exported for testing and for callers that
+ * schedule levels themselves.  All pointers are device pointers.
+ * ------------------------------------------------------------------- */
+
+/*
+ * Plain schoolbook products (the base case): `count` rows of `limbs` x
+ * `limbs` limbs, row k of A at A + k*lda, of B at Bv + k*ldb; 2*limbs limbs
+ * written at OUT + k*ldo.  limbs <= 1024.
+ */
+tc_status tc_schoolbook(size_t count, size_t limbs, const uint32_t *A, size_t lda,
+                        const uint32_t *Bv, size_t ldb, uint32_t *OUT, size_t ldo,
+                        void *stream);
+
+/*
+ * Evaluation (Section 4, eq. 4.1-4.2; points of Section 6).  Each of `count`
+ * operand rows of `limbs` limbs (row k at U + k*ld) is split into B blocks
+ * of b = ceil(limbs/B) limbs and evaluated at the 2B-1 points in the order
+ * 0, +1, -1, +2, -2, ..., +2^(B-2), -2^(B-2).  Value p of row k is written
+ * as a magnitude of `estride` limbs at OUT + (k*(2B-1) + p) * estride, and
+ * its sign (1 = negative) at SGN[k*(2B-1) + p].  estride must be >= e (the
+ * evaluation length) and a multiple of 4.
+ */
+tc_status tc_toom_evaluate(size_t count, size_t limbs, int B, const uint32_t *U, size_t ld,
+                           uint32_t *OUT, size_t estride, uint8_t *SGN, void *stream);
+
+/*
+ * Interpolation and recomposition of one level (Section 4 even-odd
+ * combine, Theorem 3.2 divided differences with exact division, Theorem 3.3
+ * Newton-to-monomial, recomposition W(2^(32 b))).  For each of `count`
+ * products of operands of `limbs` limbs: the 2B-1 pointwise products are
+ * magnitudes of 2e limbs at Y + (k*(2B-1) + p) * ystride with signs
+ * SGN_U[k*(2B-1)+p] xor SGN_V[k*(2B-1)+p] (either may be NULL = all
+ * positive); 2*limbs result limbs are written at OUT + k*ldo.  `work` is
+ * device scratch of tc_toom_interpolate_work_bytes(...) * count bytes (may be
+ * NULL when that is 0).  ystride >= 2e, multiple of 4.
+ */
+tc_status tc_toom_interpolate(size_t count, size_t limbs, int B,
+                              const uint32_t *Y, size_t ystride,
+                              const uint8_t *SGN_U, const uint8_t *SGN_V,
+                              uint32_t *OUT, size_t ldo, void *work, void *stream);
+
+/* Per-product scratch bytes of tc_toom_interpolate (0 when it runs in shared memory). */
+size_t tc_toom_interpolate_work_bytes(size_t limbs, int B);
+
+/* ---------------------------------------------------------------------
+ * Serving: a request loop on a host thread that admits products while the
+ * scratch budget and a slot allow, groups them by size class, and keeps the
+ * GPU busy with several groups in flight.  Thread-safe.
+ * ------------------------------------------------------------------- */
+
+/* Submit u*v (device pointers; they must stay valid until tc_serve_poll
+ * reports completion).  TC_EBUSY = not admitted now (retry later). */
+tc_status tc_serve_submit(tc_ctx *ctx, const uint32_t *a, size_t na, const uint32_t *b,
+                          size_t nb, uint32_t *out, uint64_t *ticket);
+
+/* TC_OK when the ticket's product is complete in `out`, TC_EPENDING while it
+ * runs, or an error status.  A completed ticket may be polled once more. */
+tc_status tc_serve_poll(tc_ctx *ctx, uint64_t ticket);
+
+/* Latency percentiles (submit -> completion seen by the loop) and sustained
+ * product-bits per second over the completed requests so far.  Product bits
+ * of a request = 32 (na + nb). */
+tc_status tc_serve_stats(tc_ctx *ctx, double *p50_ms, double *p99_ms, double *bits_per_s,
+                         uint64_t *completed);
+
+/* Stop the serving loop (pending requests complete first). */
+tc_status tc_serve_stop(tc_ctx *ctx);
+
+/* ---------------------------------------------------------------------
+ * Phase timing.  When enabled, every evaluate / base-case / interpolate
+ * launch of tc_mul* calls on this context is bracketed by CUDA events
+ * recorded on the launching stream, and its algorithmic work is recorded:
+ * bytes = limbs the step must read plus limbs it must write (x4), and
+ * limb_products = the s*s limb products of each schoolbook product.
+ * ------------------------------------------------------------------- */
+typedef struct {
+    int kind;              /* 0 evaluate, 1 base-case product, 2 interpolate+recompose */
+    int level;             /* Toom level (base case: number of levels) */
+    int launches;
+    double ms;             /* summed event time */
+    double bytes;          /* summed algorithmic bytes */
+    double limb_products;  /* summed limb products (base case only) */
+} tc_phase_stat;
+
+/* Turn phase timing on (1) or off (0); turning it on clears the records. */
+tc_status tc_profile_enable(tc_ctx *ctx, int on);
+
+/* Wait for the recorded events and report up to `cap` phases in *out
+ * (one entry per kind and level); *n receives the number written. */
+tc_status tc_profile_read(tc_ctx *ctx, tc_phase_stat *out, int cap, int *n);
+
+/* Message for a status code (static string). */
+const char *tc_strerror(tc_status s);
+
+/* cudaError_t of the last TC_EDEVICE on this thread (0 if none). */
+int tc_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TC_H */

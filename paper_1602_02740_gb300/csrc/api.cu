@@ -1,0 +1,658 @@
+// C-ABI entry points (include/tc.h): context, plans, scratch, level schedule.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/tc.h"
+#include "tc_device.cuh"
+#include "tc_internal.h"
+#include "tc_ctx.h"
+
+using namespace tc;
+
+static thread_local int g_last_cuda_error = 0;
+
+tc_status tc_fail_cuda(cudaError_t e) {
+    g_last_cuda_error = (int)e;
+    return e == cudaErrorMemoryAllocation ? TC_ENOMEM : TC_EDEVICE;
+}
+
+#define CK(x)                                         \
+    do {                                              \
+        cudaError_t _e = (x);                         \
+        if (_e != cudaSuccess) return tc_fail_cuda(_e); \
+    } while (0)
+
+extern "C" const char* tc_strerror(tc_status s) {
+    switch (s) {
+        case TC_OK: return "ok";
+        case TC_EINVAL: return "invalid argument";
+        case TC_ENOMEM: return "scratch budget exceeded or device allocation failed";
+        case TC_EBUSY: return "not admitted: budget or slots full";
+        case TC_ETIMEOUT: return "bounded wait gave up";
+        case TC_EDEVICE: return "CUDA error";
+        case TC_EPENDING: return "pending";
+    }
+    return "unknown status";
+}
+
+extern "C" int tc_last_cuda_error(void) { return g_last_cuda_error; }
+
+// ---------------------------------------------------------------------------
+// Plans
+// ---------------------------------------------------------------------------
+namespace tc {
+
+// Built-in rule: pick B per level so the recursion ends near 64-128 limbs.
+tc_opts default_plan(size_t s) {
+    tc_opts o;
+    memset(&o, 0, sizeof(o));
+    size_t L = s;
+    while (L > 128 && o.levels < TC_MAX_LEVELS) {
+        int B = L > 16384 ? 16 : L > 2048 ? 8 : L > 512 ? 4 : 3;
+        o.B[o.levels++] = B;
+        LevelGeom g = make_level((int)L, B);
+        L = (size_t)g.e;
+    }
+    return o;
+}
+
+bool plan_valid(const tc_opts& o, size_t s) {
+    if (o.levels < 0 || o.levels > TC_MAX_LEVELS) return false;
+    size_t L = s;
+    for (int l = 0; l < o.levels; ++l) {
+        if (o.B[l] < 2 || o.B[l] > 32) return false;
+        if ((size_t)o.B[l] > L) return false;
+        LevelGeom g = make_level((int)L, o.B[l]);
+        L = (size_t)g.e;
+    }
+    return L <= (size_t)LEAF_MAX;
+}
+
+tc_opts plan_for(tc_ctx* ctx, size_t s) {
+    if (ctx) {
+        for (auto& row : ctx->table)
+            if (s <= row.first && plan_valid(row.second, s)) return row.second;
+    }
+    return default_plan(s);
+}
+
+// Scratch layout of a uniform batch.
+struct BatchLayout {
+    std::vector<LevelGeom> g;
+    std::vector<long> P;          // products at each level (P[0] = count)
+    std::vector<size_t> evalU, evalV, sgnU, sgnV, prod, work;  // byte offsets
+    size_t total = 0;
+};
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+BatchLayout layout_for(size_t count, size_t s, const tc_opts& o, bool square) {
+    BatchLayout L;
+    size_t off = 0;
+    long P = (long)count;
+    int sl = (int)s;
+    for (int l = 0; l < o.levels; ++l) {
+        LevelGeom g = make_level(sl, o.B[l]);
+        const long Pn = P * (2 * g.B - 1);
+        L.g.push_back(g);
+        L.P.push_back(P);
+        L.evalU.push_back(off); off = align256(off + (size_t)Pn * g.estride * 4);
+        L.evalV.push_back(off); if (!square) off = align256(off + (size_t)Pn * g.estride * 4);
+        L.sgnU.push_back(off); off = align256(off + (size_t)Pn);
+        L.sgnV.push_back(off); if (!square) off = align256(off + (size_t)Pn);
+        L.prod.push_back(off); off = align256(off + (size_t)Pn * g.ystride * 4);
+        L.work.push_back(off); off = align256(off + (size_t)P * interp_work_bytes(g));
+        P = Pn;
+        sl = g.e;
+    }
+    L.P.push_back(P);
+    L.total = off;
+    return L;
+}
+
+tc_status ensure_arena(tc_ctx* ctx, size_t bytes, cudaStream_t st) {
+    if (bytes <= ctx->arena_bytes) return TC_OK;
+    if (bytes > ctx->budget) return TC_ENOMEM;
+    CK(cudaStreamSynchronize(st));
+    if (ctx->arena) cudaFree(ctx->arena);
+    ctx->arena = nullptr;
+    ctx->arena_bytes = 0;
+    size_t want = std::min(ctx->budget, std::max(bytes, bytes + bytes / 4));
+    cudaError_t e = cudaMalloc(&ctx->arena, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        e = cudaMalloc(&ctx->arena, bytes);
+        if (e != cudaSuccess) { cudaGetLastError(); ctx->arena = nullptr; return TC_ENOMEM; }
+        want = bytes;
+    }
+    ctx->arena_bytes = want;
+    return TC_OK;
+}
+
+// Phase timing: events around each launch when the context asks for it.
+struct PhaseTimer {
+    tc_ctx* ctx;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr;
+    int kind = 0, level = 0;
+    double bytes = 0, lp = 0;
+    static cudaEvent_t get(tc_ctx* c) {
+        if (!c->event_pool.empty()) {
+            cudaEvent_t e = c->event_pool.back();
+            c->event_pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+    void begin(int k, int l, double by, double p) {
+        if (!ctx || !ctx->profile) return;
+        kind = k; level = l; bytes = by; lp = p;
+        a = get(ctx);
+        cudaEventRecord(a, st);
+    }
+    void end() {
+        if (!ctx || !ctx->profile || !a) return;
+        cudaEvent_t b = get(ctx);
+        cudaEventRecord(b, st);
+        ctx->recs.push_back({kind, level, a, b, bytes, lp});
+        a = nullptr;
+    }
+};
+
+// Run a uniform batch whose scratch is `base` laid out by `L`.
+tc_status run_uniform(const BatchLayout& L, char* base, size_t count, size_t s, const u32* A,
+                      long lda, const u32* Bm, long ldb, u32* OUT, long ldo, bool square,
+                      cudaStream_t st, tc_ctx* ctx) {
+    PhaseTimer pt{ctx, st};
+    const int D = (int)L.g.size();
+    if (D == 0) {
+        pt.begin(1, 0, 4.0 * count * 4 * s, (double)count * s * s);
+        CK(launch_leaf(A, lda, square ? A : Bm, square ? lda : ldb, OUT, ldo, (int)s, (long)count, st));
+        pt.end();
+        return TC_OK;
+    }
+    const u32* inU = A;
+    const u32* inV = square ? A : Bm;
+    long strU = lda, strV = square ? lda : ldb;
+    for (int l = 0; l < D; ++l) {
+        const LevelGeom& g = L.g[l];
+        u32* eU = reinterpret_cast<u32*>(base + L.evalU[l]);
+        uint8_t* sU = reinterpret_cast<uint8_t*>(base + L.sgnU[l]);
+        const double eval_bytes = 4.0 * L.P[l] * (g.s + (2.0 * g.B - 1) * g.estride) +
+                                  (2.0 * g.B - 1) * L.P[l];
+        pt.begin(0, l, eval_bytes, 0);
+        CK(launch_eval(inU, strU, g, eU, sU, L.P[l], st));
+        pt.end();
+        inU = eU;
+        strU = g.estride;
+        if (!square) {
+            u32* eV = reinterpret_cast<u32*>(base + L.evalV[l]);
+            uint8_t* sV = reinterpret_cast<uint8_t*>(base + L.sgnV[l]);
+            pt.begin(0, l, eval_bytes, 0);
+            CK(launch_eval(inV, strV, g, eV, sV, L.P[l], st));
+            pt.end();
+            inV = eV;
+            strV = g.estride;
+        } else {
+            inV = inU;
+            strV = strU;
+        }
+    }
+    const LevelGeom& gl = L.g[D - 1];
+    pt.begin(1, D, 4.0 * L.P[D] * 4 * gl.e, (double)L.P[D] * gl.e * gl.e);
+    CK(launch_leaf(inU, strU, inV, strV, reinterpret_cast<u32*>(base + L.prod[D - 1]), gl.ystride,
+                   gl.e, L.P[D], st));
+    pt.end();
+    for (int l = D - 1; l >= 0; --l) {
+        const LevelGeom& g = L.g[l];
+        u32* out;
+        long ostr;
+        if (l == 0) {
+            out = OUT;
+            ostr = ldo;
+        } else {
+            out = reinterpret_cast<u32*>(base + L.prod[l - 1]);
+            ostr = L.g[l - 1].ystride;
+        }
+        // squaring: every pointwise product U(x)^2 is non-negative, so no signs are passed
+        const uint8_t* sU = square ? nullptr : reinterpret_cast<const uint8_t*>(base + L.sgnU[l]);
+        const uint8_t* sV = square ? nullptr : reinterpret_cast<const uint8_t*>(base + L.sgnV[l]);
+        u32* work = interp_work_bytes(g) ? reinterpret_cast<u32*>(base + L.work[l]) : nullptr;
+        pt.begin(2, l, 4.0 * L.P[l] * ((2.0 * g.B - 1) * 2 * g.e + 2.0 * g.s) +
+                           (square ? 0.0 : 2.0 * (2 * g.B - 1) * L.P[l]), 0);
+        CK(launch_interp(g, reinterpret_cast<const u32*>(base + L.prod[l]), sU, sV, out, ostr,
+                         2 * g.s, work, L.P[l], st));
+        pt.end();
+    }
+    return TC_OK;
+}
+
+}  // namespace tc
+
+// ---------------------------------------------------------------------------
+// Context
+// ---------------------------------------------------------------------------
+static bool load_table(const char* path, std::vector<std::pair<size_t, tc_opts>>& out) {
+    FILE* f = fopen(path, "r");
+    if (!f) return false;
+    char line[512];
+    while (fgets(line, sizeof line, f)) {
+        if (line[0] == '#' || line[0] == '\n') continue;
+        unsigned long long mx;
+        int lv, n = 0, pos = 0;
+        if (sscanf(line, "%llu %d%n", &mx, &lv, &n) != 2) continue;
+        pos = n;
+        tc_opts o;
+        memset(&o, 0, sizeof o);
+        if (lv < 0 || lv > TC_MAX_LEVELS) continue;
+        o.levels = lv;
+        bool ok = true;
+        for (int l = 0; l < lv; ++l) {
+            if (sscanf(line + pos, "%d%n", &o.B[l], &n) != 1) { ok = false; break; }
+            pos += n;
+        }
+        if (ok) out.push_back({(size_t)mx, o});
+    }
+    fclose(f);
+    return true;
+}
+
+extern "C" tc_status tc_create(tc_ctx** ctx, int device, size_t hbm_budget_bytes,
+                               const char* tune_table_path) {
+    if (!ctx) return TC_EINVAL;
+    *ctx = nullptr;
+    int ndev = 0;
+    CK(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return TC_EINVAL;
+    CK(cudaSetDevice(device));
+    size_t fr = 0, tot = 0;
+    CK(cudaMemGetInfo(&fr, &tot));
+    tc_ctx* c = new tc_ctx();
+    c->device = device;
+    c->budget = hbm_budget_bytes ? hbm_budget_bytes : fr / 4 * 3;
+    if (tune_table_path && !load_table(tune_table_path, c->table)) {
+        delete c;
+        return TC_EINVAL;
+    }
+    *ctx = c;
+    return TC_OK;
+}
+
+extern "C" void tc_destroy(tc_ctx* ctx) {
+    if (!ctx) return;
+    tc_serve_stop(ctx);
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    for (auto& r : ctx->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    for (auto e : ctx->event_pool) cudaEventDestroy(e);
+    if (ctx->arena) cudaFree(ctx->arena);
+    if (ctx->aux) cudaFree(ctx->aux);
+    delete ctx;
+}
+
+extern "C" tc_status tc_plan_for(tc_ctx* ctx, size_t limbs, tc_opts* plan_out) {
+    if (!plan_out || limbs == 0) return TC_EINVAL;
+    *plan_out = plan_for(ctx, limbs);
+    return TC_OK;
+}
+
+static tc_status resolve_plan(tc_ctx* ctx, size_t s, const tc_opts* opts, tc_opts& o) {
+    o = opts ? *opts : plan_for(ctx, s);
+    return plan_valid(o, s) ? TC_OK : TC_EINVAL;
+}
+
+extern "C" tc_status tc_scratch_bytes(tc_ctx* ctx, size_t count, size_t limbs, const tc_opts* opts,
+                                      size_t* bytes_out) {
+    if (!bytes_out || limbs == 0) return TC_EINVAL;
+    tc_opts o;
+    tc_status s = resolve_plan(ctx, limbs, opts, o);
+    if (s) return s;
+    *bytes_out = layout_for(count, limbs, o, false).total;
+    return TC_OK;
+}
+
+// Uniform batch with the context's arena.
+static tc_status mul_uniform(tc_ctx* ctx, size_t count, size_t limbs, const u32* A, size_t lda,
+                             const u32* Bm, size_t ldb, u32* OUT, size_t ldo, const tc_opts* opts,
+                             bool square, cudaStream_t st) {
+    if (count == 0) return TC_OK;
+    if (limbs == 0) return TC_OK;  // products of zero limbs have zero limbs
+    tc_opts o;
+    tc_status s = resolve_plan(ctx, limbs, opts, o);
+    if (s) return s;
+    BatchLayout L = layout_for(count, limbs, o, square);
+    s = ensure_arena(ctx, L.total, st);
+    if (s) return s;
+    return run_uniform(L, (char*)ctx->arena, count, limbs, A, (long)lda, Bm, (long)ldb, OUT,
+                       (long)ldo, square, st, ctx);
+}
+
+extern "C" tc_status tc_mul_uniform(tc_ctx* ctx, size_t count, size_t limbs, const uint32_t* A,
+                                    size_t lda, const uint32_t* Bv, size_t ldb, uint32_t* OUT,
+                                    size_t ldo, const tc_opts* opts, void* stream) {
+    if (!ctx || (count && (!A || !Bv || !OUT))) return TC_EINVAL;
+    if (count > 1 && (lda < limbs || ldb < limbs || ldo < 2 * limbs)) return TC_EINVAL;
+    CK(cudaSetDevice(ctx->device));
+    const bool sq = (A == Bv && lda == ldb);
+    return mul_uniform(ctx, count, limbs, A, lda, Bv, ldb, OUT, ldo, opts, sq, (cudaStream_t)stream);
+}
+
+extern "C" tc_status tc_mul_uniform_host(tc_ctx* ctx, size_t count, size_t limbs,
+                                         const uint32_t* A, const uint32_t* Bv, uint32_t* OUT,
+                                         const tc_opts* opts, void* stream) {
+    if (!ctx || (count && (!A || !Bv || !OUT))) return TC_EINVAL;
+    if (count == 0) return TC_OK;
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t in_bytes = count * limbs * 4, out_bytes = count * 2 * limbs * 4;
+    const size_t need = 2 * align256(in_bytes) + align256(out_bytes);
+    if (need > ctx->aux_bytes) {
+        CK(cudaStreamSynchronize(st));
+        if (ctx->aux) cudaFree(ctx->aux);
+        ctx->aux = nullptr;
+        ctx->aux_bytes = 0;
+        if (need > ctx->budget) return TC_ENOMEM;
+        cudaError_t e = cudaMalloc(&ctx->aux, need);
+        if (e != cudaSuccess) { cudaGetLastError(); return TC_ENOMEM; }
+        ctx->aux_bytes = need;
+    }
+    char* base = (char*)ctx->aux;
+    u32* dA = (u32*)base;
+    u32* dB = (u32*)(base + align256(in_bytes));
+    u32* dO = (u32*)(base + 2 * align256(in_bytes));
+    CK(cudaMemcpyAsync(dA, A, in_bytes, cudaMemcpyHostToDevice, st));
+    if (Bv != A) CK(cudaMemcpyAsync(dB, Bv, in_bytes, cudaMemcpyHostToDevice, st));
+    tc_status s = mul_uniform(ctx, count, limbs, dA, limbs, Bv == A ? dA : dB, limbs, dO,
+                              2 * limbs, opts, Bv == A, st);
+    if (s) return s;
+    CK(cudaMemcpyAsync(OUT, dO, out_bytes, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return TC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// General products: gather into padded rows per size class, run, scatter.
+// ---------------------------------------------------------------------------
+namespace {
+
+__global__ void gather_rows(const u32* src, const int64_t* off, const int64_t* len, int s,
+                            u32* dst, int count) {
+    const int k = blockIdx.y;
+    if (k >= count) return;
+    const u32* a = src + off[k];
+    const int64_t L = len[k];
+    u32* d = dst + (long)k * s;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < s; i += gridDim.x * blockDim.x)
+        d[i] = i < L ? a[i] : 0u;
+}
+
+__global__ void scatter_rows(const u32* src, int stride, const int64_t* off, const int64_t* len,
+                             u32* dst, int count) {
+    const int k = blockIdx.y;
+    if (k >= count) return;
+    const u32* s = src + (long)k * stride;
+    u32* d = dst + off[k];
+    const int64_t L = len[k];
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < L; i += (long)gridDim.x * blockDim.x)
+        d[i] = s[i];
+}
+
+size_t size_class(size_t L) {
+    // classes 2^k and 3 * 2^(k-1): at most 50% padding
+    size_t c = 32;
+    while (c < L) {
+        size_t mid = c + c / 2;
+        if (mid >= L) return mid;
+        c *= 2;
+    }
+    return c;
+}
+
+}  // namespace
+
+// Products listed by (offset, length) triples; all device limb buffers, host index arrays.
+static tc_status mul_general(tc_ctx* ctx, size_t count, const u32* A, const int64_t* a_off,
+                             const int64_t* a_len, const u32* Bm, const int64_t* b_off,
+                             const int64_t* b_len, u32* OUT, const int64_t* out_off,
+                             const tc_opts* opts, cudaStream_t st) {
+    // classes by padded balanced length
+    struct Item { size_t k, cls; };
+    std::vector<Item> items;
+    items.reserve(count);
+    for (size_t k = 0; k < count; ++k) {
+        if (a_len[k] < 0 || b_len[k] < 0) return TC_EINVAL;
+        const size_t L = (size_t)std::max(a_len[k], b_len[k]);
+        if (a_len[k] == 0 || b_len[k] == 0) {
+            const size_t n = (size_t)(a_len[k] + b_len[k]);
+            if (n) CK(cudaMemsetAsync(OUT + out_off[k], 0, n * 4, st));
+            continue;
+        }
+        items.push_back({k, size_class(L)});
+    }
+    std::sort(items.begin(), items.end(), [](const Item& x, const Item& y) { return x.cls < y.cls; });
+    size_t i = 0;
+    while (i < items.size()) {
+        size_t j = i;
+        while (j < items.size() && items[j].cls == items[i].cls) ++j;
+        const size_t s = items[i].cls, cnt = j - i;
+        // a caller's plan applies to every size class it is valid for
+        tc_opts o = (opts && plan_valid(*opts, s)) ? *opts : plan_for(ctx, s);
+        BatchLayout L = layout_for(cnt, s, o, false);
+        // index arrays + padded rows + outputs after the level scratch
+        const size_t idx_bytes = align256(cnt * 8);
+        const size_t rows_bytes = align256(cnt * s * 4);
+        const size_t outs_bytes = align256(cnt * 2 * s * 4);
+        const size_t extra = 5 * idx_bytes + 2 * rows_bytes + outs_bytes;
+        tc_status e = ensure_arena(ctx, L.total + extra, st);
+        if (e) return e;
+        char* base = (char*)ctx->arena;
+        char* x = base + L.total;
+        int64_t* d_aoff = (int64_t*)x; x += idx_bytes;
+        int64_t* d_alen = (int64_t*)x; x += idx_bytes;
+        int64_t* d_boff = (int64_t*)x; x += idx_bytes;
+        int64_t* d_blen = (int64_t*)x; x += idx_bytes;
+        int64_t* d_ooff = (int64_t*)x; x += idx_bytes;
+        u32* rA = (u32*)x; x += rows_bytes;
+        u32* rB = (u32*)x; x += rows_bytes;
+        u32* rO = (u32*)x;
+        std::vector<int64_t> h(5 * cnt);
+        for (size_t t = 0; t < cnt; ++t) {
+            const size_t k = items[i + t].k;
+            h[t] = a_off[k];
+            h[cnt + t] = a_len[k];
+            h[2 * cnt + t] = b_off[k];
+            h[3 * cnt + t] = b_len[k];
+            h[4 * cnt + t] = out_off[k];
+        }
+        // pageable copies are synchronous with respect to the host buffer: safe for `h`
+        CK(cudaMemcpyAsync(d_aoff, h.data(), cnt * 8, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(d_alen, h.data() + cnt, cnt * 8, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(d_boff, h.data() + 2 * cnt, cnt * 8, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(d_blen, h.data() + 3 * cnt, cnt * 8, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(d_ooff, h.data() + 4 * cnt, cnt * 8, cudaMemcpyHostToDevice, st));
+        for (size_t c0 = 0; c0 < cnt; c0 += 65535) {
+            const int cc = (int)std::min<size_t>(65535, cnt - c0);
+            dim3 grid((unsigned)std::min<size_t>((s + 255) / 256, 64), cc);
+            gather_rows<<<grid, 256, 0, st>>>(A, d_aoff + c0, d_alen + c0, (int)s, rA + c0 * s, cc);
+            gather_rows<<<grid, 256, 0, st>>>(Bm, d_boff + c0, d_blen + c0, (int)s, rB + c0 * s, cc);
+        }
+        CK(cudaGetLastError());
+        e = run_uniform(L, base, cnt, s, rA, (long)s, rB, (long)s, rO, (long)(2 * s), false, st, ctx);
+        if (e) return e;
+        // out length per product = a_len + b_len: reuse d_alen as a scratch? compute on host
+        std::vector<int64_t> olen(cnt);
+        for (size_t t = 0; t < cnt; ++t) olen[t] = h[cnt + t] + h[3 * cnt + t];
+        CK(cudaMemcpyAsync(d_alen, olen.data(), cnt * 8, cudaMemcpyHostToDevice, st));
+        for (size_t c0 = 0; c0 < cnt; c0 += 65535) {
+            const int cc = (int)std::min<size_t>(65535, cnt - c0);
+            dim3 grid((unsigned)std::min<size_t>((2 * s + 255) / 256, 64), cc);
+            scatter_rows<<<grid, 256, 0, st>>>(rO + c0 * 2 * s, (int)(2 * s), d_ooff + c0,
+                                               d_alen + c0, OUT, cc);
+        }
+        CK(cudaGetLastError());
+        // the host vectors die at scope end: make sure the copies have consumed them
+        CK(cudaStreamSynchronize(st));
+        i = j;
+    }
+    return TC_OK;
+}
+
+extern "C" tc_status tc_mul_batch(tc_ctx* ctx, size_t count, const uint32_t* A, const int64_t* a_off,
+                                  const int64_t* a_len, const uint32_t* Bv, const int64_t* b_off,
+                                  const int64_t* b_len, uint32_t* OUT, const int64_t* out_off,
+                                  const tc_opts* opts, void* stream) {
+    if (!ctx) return TC_EINVAL;
+    if (count == 0) return TC_OK;
+    if (!A || !Bv || !OUT || !a_off || !a_len || !b_off || !b_len || !out_off) return TC_EINVAL;
+    CK(cudaSetDevice(ctx->device));
+    return mul_general(ctx, count, A, a_off, a_len, Bv, b_off, b_len, OUT, out_off, opts,
+                       (cudaStream_t)stream);
+}
+
+extern "C" tc_status tc_mul(tc_ctx* ctx, const uint32_t* a, size_t na, const uint32_t* b, size_t nb,
+                            uint32_t* out, const tc_opts* opts, void* stream) {
+    if (!ctx || !out || (na && !a) || (nb && !b)) return TC_EINVAL;
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    if (na == 0 || nb == 0) {
+        if (na + nb) CK(cudaMemsetAsync(out, 0, (na + nb) * 4, st));
+        return TC_OK;
+    }
+    if (na == nb) {
+        const bool sq = (a == b);
+        return mul_uniform(ctx, 1, na, a, na, b, nb, out, 2 * na, opts, sq, st);
+    }
+    const size_t lo = std::min(na, nb), hi = std::max(na, nb);
+    const uint32_t* longp = na >= nb ? a : b;
+    const uint32_t* shortp = na >= nb ? b : a;
+    if (hi < 2 * lo) {
+        int64_t ao = 0, al = (int64_t)na, bo = 0, bl = (int64_t)nb, oo = 0;
+        return mul_general(ctx, 1, a, &ao, &al, b, &bo, &bl, out, &oo, opts, st);
+    }
+    // slices of the longer operand, each lo limbs (last one shorter), as one batch
+    const size_t pieces = (hi + lo - 1) / lo;
+    // one uniform batch of `pieces` products lo x lo (the short operand replicated by stride 0)
+    tc_opts o;
+    tc_status s = resolve_plan(ctx, lo, opts, o);
+    if (s) return s;
+    BatchLayout L = layout_for(pieces, lo, o, false);
+    const size_t rows_bytes = align256(pieces * lo * 4);
+    const size_t outs_bytes = align256(pieces * 2 * lo * 4);
+    s = ensure_arena(ctx, L.total + rows_bytes + outs_bytes, st);
+    if (s) return s;
+    char* base = (char*)ctx->arena;
+    u32* rA = (u32*)(base + L.total);
+    u32* rO = (u32*)(base + L.total + rows_bytes);
+    CK(cudaMemsetAsync(rA, 0, pieces * lo * 4, st));
+    CK(cudaMemcpyAsync(rA, longp, hi * 4, cudaMemcpyDeviceToDevice, st));
+    s = run_uniform(L, base, pieces, lo, rA, (long)lo, shortp, 0, rO, (long)(2 * lo), false, st, ctx);
+    if (s) return s;
+    CK(launch_overlap_add(rO, (long)(2 * lo), (int)(2 * lo), (int)pieces, (long)lo, out,
+                          (long)(na + nb), st));
+    return TC_OK;
+}
+
+extern "C" tc_status tc_sqr(tc_ctx* ctx, const uint32_t* a, size_t na, uint32_t* out,
+                            const tc_opts* opts, void* stream) {
+    return tc_mul(ctx, a, na, a, na, out, opts, stream);
+}
+
+// ---------------------------------------------------------------------------
+// Steps of one level
+// ---------------------------------------------------------------------------
+extern "C" tc_status tc_schoolbook(size_t count, size_t limbs, const uint32_t* A, size_t lda,
+                                   const uint32_t* Bv, size_t ldb, uint32_t* OUT, size_t ldo,
+                                   void* stream) {
+    if (count == 0) return TC_OK;
+    if (!A || !Bv || !OUT || limbs == 0 || limbs > (size_t)LEAF_MAX) return TC_EINVAL;
+    if (count > 1 && (lda < limbs || ldb < limbs || ldo < 2 * limbs)) return TC_EINVAL;
+    CK(launch_leaf(A, (long)lda, Bv, (long)ldb, OUT, (long)ldo, (int)limbs, (long)count,
+                   (cudaStream_t)stream));
+    return TC_OK;
+}
+
+extern "C" tc_status tc_toom_evaluate(size_t count, size_t limbs, int B, const uint32_t* U,
+                                      size_t ld, uint32_t* OUT, size_t estride, uint8_t* SGN,
+                                      void* stream) {
+    if (count == 0) return TC_OK;
+    if (!U || !OUT || !SGN || B < 2 || B > 32 || limbs == 0 || limbs > (1u << 30))
+        return TC_EINVAL;
+    LevelGeom g = make_level((int)limbs, B);
+    if (estride < (size_t)g.e || estride % 4) return TC_EINVAL;
+    if (count > 1 && ld < limbs) return TC_EINVAL;
+    g.estride = (int)estride;
+    CK(launch_eval(U, (long)ld, g, OUT, SGN, (long)count, (cudaStream_t)stream));
+    return TC_OK;
+}
+
+extern "C" size_t tc_toom_interpolate_work_bytes(size_t limbs, int B) {
+    if (B < 2 || B > 32 || limbs == 0) return 0;
+    return interp_work_bytes(make_level((int)limbs, B));
+}
+
+extern "C" tc_status tc_toom_interpolate(size_t count, size_t limbs, int B, const uint32_t* Y,
+                                         size_t ystride, const uint8_t* SGN_U,
+                                         const uint8_t* SGN_V, uint32_t* OUT, size_t ldo,
+                                         void* work, void* stream) {
+    if (count == 0) return TC_OK;
+    if (!Y || !OUT || B < 2 || B > 32 || limbs == 0 || limbs > (1u << 30)) return TC_EINVAL;
+    LevelGeom g = make_level((int)limbs, B);
+    if (ystride < (size_t)(2 * g.e) || ystride % 4) return TC_EINVAL;
+    if (count > 1 && ldo < 2 * limbs) return TC_EINVAL;
+    if (interp_work_bytes(g) && !work) return TC_EINVAL;
+    g.ystride = (int)ystride;
+    CK(launch_interp(g, Y, SGN_U, SGN_V, OUT, (long)ldo, 2 * g.s, (u32*)work, (long)count,
+                     (cudaStream_t)stream));
+    return TC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Phase timing
+// ---------------------------------------------------------------------------
+extern "C" tc_status tc_profile_enable(tc_ctx* ctx, int on) {
+    if (!ctx) return TC_EINVAL;
+    CK(cudaSetDevice(ctx->device));
+    for (auto& r : ctx->recs) {
+        cudaEventSynchronize(r.b);
+        ctx->event_pool.push_back(r.a);
+        ctx->event_pool.push_back(r.b);
+    }
+    ctx->recs.clear();
+    ctx->profile = on != 0;
+    return TC_OK;
+}
+
+extern "C" tc_status tc_profile_read(tc_ctx* ctx, tc_phase_stat* out, int cap, int* n) {
+    if (!ctx || !n || (cap > 0 && !out)) return TC_EINVAL;
+    CK(cudaSetDevice(ctx->device));
+    std::vector<tc_phase_stat> acc;
+    for (auto& r : ctx->recs) {
+        CK(cudaEventSynchronize(r.b));
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, r.a, r.b));
+        tc_phase_stat* p = nullptr;
+        for (auto& x : acc)
+            if (x.kind == r.kind && x.level == r.level) p = &x;
+        if (!p) {
+            acc.push_back({r.kind, r.level, 0, 0.0, 0.0, 0.0});
+            p = &acc.back();
+        }
+        p->launches += 1;
+        p->ms += ms;
+        p->bytes += r.bytes;
+        p->limb_products += r.lp;
+    }
+    std::sort(acc.begin(), acc.end(), [](const tc_phase_stat& x, const tc_phase_stat& y) {
+        return x.kind != y.kind ? x.kind < y.kind : x.level < y.level;
+    });
+    int k = 0;
+    for (; k < cap && k < (int)acc.size(); ++k) out[k] = acc[k];
+    *n = k;
+    return TC_OK;
+}

@@ -1,0 +1,48 @@
+// Internal host-side interface between the C-ABI layer and the kernel files.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace tc {
+
+// Geometry of one Toom level for operands of s limbs split into B blocks.
+struct LevelGeom {
+    int B, n;      // blocks, degree n = B - 1
+    int s;         // operand length (limbs)
+    int b;         // block size = ceil(s / B)
+    int e;         // evaluation length = b + ceil((n(n-1)+1)/32)
+    int estride;   // evaluation row stride: roundup(e, 4)
+    int ystride;   // pointwise-product row stride: roundup(2e, 4)
+    int Y;         // interpolation value length: roundup(2e + 2, 128)
+};
+
+LevelGeom make_level(int s, int B);
+
+// Exact-division constants of the Newton loops, passed by value to kernels.
+struct DivTable;
+
+// Largest operand length the base-case kernel accepts.
+constexpr int LEAF_MAX = 1024;
+
+cudaError_t launch_leaf(const uint32_t* A, long lda, const uint32_t* Bm, long ldb,
+                        uint32_t* OUT, long ldo, int s, long P, cudaStream_t st);
+
+cudaError_t launch_eval(const uint32_t* in, long in_stride, const LevelGeom& g,
+                        uint32_t* out, uint8_t* sgn, long P, cudaStream_t st);
+
+// Per-product bytes of global work the interpolation needs (0 = shared memory).
+size_t interp_work_bytes(const LevelGeom& g);
+
+cudaError_t launch_interp(const LevelGeom& g, const uint32_t* y, const uint8_t* su,
+                          const uint8_t* sv, uint32_t* out, long out_stride, int out_len,
+                          uint32_t* work, long P, cudaStream_t st);
+
+// out[0 .. out_len) = sum_k w_k 2^(32 off k), w_k = rows[k*row_stride .. + row_len),
+// for `count` terms; one output (single CTA).  Used to add sliced partial products.
+cudaError_t launch_overlap_add(const uint32_t* rows, long row_stride, int row_len, long count,
+                               long off, uint32_t* out, long out_len, cudaStream_t st);
+
+cudaError_t launch_zero(uint32_t* p, size_t n, cudaStream_t st);
+
+}  // namespace tc

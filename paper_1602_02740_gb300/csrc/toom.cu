@@ -1,0 +1,617 @@
+// One Toom-Cook level on the GPU: evaluation, interpolation, recomposition.
+//
+// Level geometry (all lengths in 32-bit limbs): operands of s limbs are cut
+// into B blocks of b = ceil(s/B) limbs (Section 1, eq. 1.1-1.3; the top block
+// is zero-padded).  Evaluation values have e = b + ceil((n(n-1)+1)/32) limbs,
+// pointwise products 2e limbs, and interpolation values Y >= 2e + 2 limbs.
+//
+// Points (Section 6): x = 0 and x = +-2^j, j = 0..n-1, stored in the order
+// 0, +1, -1, +2, -2, ...; signed values are sign-magnitude.
+#include "tc_device.cuh"
+#include "tc_internal.h"
+
+namespace tc {
+
+LevelGeom make_level(int s, int B) {
+    LevelGeom g;
+    g.B = B;
+    g.n = B - 1;
+    g.s = s;
+    g.b = (s + B - 1) / B;
+    g.e = g.b + (g.n * (g.n - 1) + 1 + 31) / 32;
+    g.estride = (g.e + 3) / 4 * 4;
+    g.ystride = (2 * g.e + 3) / 4 * 4;
+    g.Y = (2 * g.e + 2 + CH - 1) / CH * CH;
+    return g;
+}
+
+// ===========================================================================
+// Evaluation (Section 4, eq. 4.1-4.2).
+//
+// For x = 2^j the even part E = sum_{i even} u_i 2^(j i) and the odd part
+// O = sum_{i odd} u_i 2^(j i) are formed column by column (each block shifted
+// by j i bits), then U(x) = E + O and |U(-x)| = |E - O|.  The sign of E - O
+// is decided first by a scan from the top limb down (it almost always
+// settles on the first limb), so the magnitude is produced in one bottom-up
+// pass with no negation afterwards.  Warp j handles x = 2^j.
+// ===========================================================================
+
+__device__ __forceinline__ u32 blk(const u32* row, int s, int b, int i, int x) {
+    const int g = i * b + x;
+    return (x >= 0 && x < b && g < s) ? __ldg(row + g) : 0u;
+}
+
+// Column sums of E and O at output limb l for x = 2^j.
+__device__ __forceinline__ void eval_cols(const u32* row, int s, int B, int b, int j, int l,
+                                          i64& E, i64& O) {
+    u64 e = 0, o = 0;
+    for (int i = 0; i < B; ++i) {
+        const int sh = j * i;
+        const int qa = sh >> 5, r = sh & 31;
+        const u32 hi = blk(row, s, b, i, l - qa);
+        const u32 lo = blk(row, s, b, i, l - qa - 1);
+        const u32 t = fshl(lo, hi, (u32)r);
+        if (i & 1) o += t; else e += t;
+    }
+    E = (i64)e;
+    O = (i64)o;
+}
+
+__global__ void __launch_bounds__(1024)
+eval_kernel(const u32* __restrict__ in, long in_stride, LevelGeom g, u32* __restrict__ out,
+            uint8_t* __restrict__ sgn, long P) {
+    const long k = blockIdx.x;
+    if (k >= P) return;
+    const u32* row = in + k * in_stride;
+    const int npts = 2 * g.B - 1;
+    u32* orow0 = out + (k * npts) * (long)g.estride;
+    const int tid = threadIdx.x;
+    // point 0: U(0) = u_0
+    for (int i = tid; i < g.estride; i += blockDim.x) orow0[i] = (i < g.b && i < g.s) ? row[i] : 0u;
+    if (tid == 0) sgn[k * npts] = 0;
+
+    const int warp = tid >> 5, lane = tid & 31;
+    const int nw = blockDim.x >> 5;
+    for (int j = warp; j < g.n; j += nw) {
+        // ---- sign of E - O, top-down ----
+        i64 T = 0;
+        int sign = 0;
+        for (int top = g.e - 1; top >= 0 && sign == 0; top -= 32) {
+            const int l = top - lane;
+            i64 d = 0;
+            if (l >= 0) {
+                i64 E, O;
+                eval_cols(row, g.s, g.B, g.b, j, l, E, O);
+                d = E - O;
+            }
+            const unsigned nz = __ballot_sync(FULL, d != 0);
+            if (T == 0 && nz == 0) continue;
+            for (int t = 0; t < 32; ++t) {
+                const i64 dt = __shfl_sync(FULL, d, t);
+                if (top - t < 0) break;
+                T = T * 4294967296LL + dt;
+                if (T >= 17) { sign = 1; break; }
+                if (T <= -17) { sign = -1; break; }
+            }
+        }
+        if (sign == 0) sign = T < 0 ? -1 : 1;
+
+        u32* rp = out + (k * npts + 2 * j + 1) * (long)g.estride;
+        u32* rm = out + (k * npts + 2 * j + 2) * (long)g.estride;
+        SignedNorm sp{0, 0}, smn{0, 0};
+        for (int base = 0; base < g.estride; base += CH) {
+            i64 cp[4], cm[4];
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) {
+                const int l = base + 4 * lane + jj;
+                i64 E = 0, O = 0;
+                if (l < g.e) eval_cols(row, g.s, g.B, g.b, j, l, E, O);
+                cp[jj] = E + O;
+                cm[jj] = sign > 0 ? E - O : O - E;
+            }
+            u32 dp[4], dm[4];
+            warp_norm_signed(cp, sp, dp);
+            warp_norm_signed(cm, smn, dm);
+            const int pos = base + 4 * lane;
+            if (pos < g.estride) {  // estride is a multiple of 4
+                st4(rp + pos, dp);
+                st4(rm + pos, dm);
+            }
+        }
+        if (lane == 0) {
+            sgn[k * npts + 2 * j + 1] = 0;
+            sgn[k * npts + 2 * j + 2] = sign < 0 ? 1 : 0;
+        }
+    }
+}
+
+cudaError_t launch_eval(const u32* in, long in_stride, const LevelGeom& g, u32* out,
+                        uint8_t* sgn, long P, cudaStream_t st) {
+    if (P <= 0) return cudaSuccess;
+    int warps = g.n < 1 ? 1 : g.n;
+    if (warps > 32) warps = 32;
+    eval_kernel<<<(unsigned)P, warps * 32, 0, st>>>(in, in_stride, g, out, sgn, P);
+    return cudaGetLastError();
+}
+
+// ===========================================================================
+// Interpolation (Sections 3 and 4).
+//
+// Values of W_e and X W_o at the nodes X = 0, 1, 4, ..., 4^(n-1) are formed
+// by the even-odd combine, then both polynomials go through the two Newton
+// double loops.  Within one stage of a loop every update reads only values of
+// the previous stage, so a stage is a set of independent "chains", each a
+// pass over Y limbs run by one warp; stages are separated by __syncthreads.
+// Each value has two slots (ping-pong) so a stage never overwrites a value
+// another chain of the same stage still reads.
+//
+//   loop 1, stage k (Theorem 3.2): c[m] = (c[m] - c[m-1]) / (X[m] - X[m-k]),
+//     m = k..n.  For m = k the divisor is 4^(m-1) (a shift); otherwise it is
+//     4^(m-k-1) (4^k - 1): a right shift, then exact division by the odd
+//     4^k - 1 (two 32-bit divisions 2^k - 1 and 2^k + 1 when k >= 16).
+//   loop 2, stage m (Theorem 3.3): c[k] -= X[m] c[k+1], k = m..n-1, i.e.
+//     a subtraction of c[k+1] shifted left by 2(m-1).  Stage m = 0 is empty
+//     because X[0] = 0.
+//
+// Right shifts need the limbs above, so those chains emit chunk c-1 while
+// loading chunk c (a one-chunk lag); stores stay 16-byte aligned.
+// ===========================================================================
+
+struct DivTable {
+    DivConst d[2][32];  // [first/second divisor][k]; d == 1 means none
+};
+
+static u32 inv32(u32 d) {
+    u32 x = d;  // correct to 3 bits for odd d
+    for (int i = 0; i < 5; ++i) x *= 2u - d * x;
+    return x;
+}
+
+static u32 powmod_host(u64 base, u64 e, u32 m) {
+    u64 r = 1 % m;
+    base %= m;
+    while (e) {
+        if (e & 1) r = r * base % m;
+        base = base * base % m;
+        e >>= 1;
+    }
+    return (u32)r;
+}
+
+static DivConst make_div(u32 d) {
+    DivConst c;
+    c.d = d;
+    c.inv = inv32(d);
+    c.magic = d > 1 ? ~0ull / d : 0ull;
+    if (d > 1) {
+        // rk[0] = rho^4 = 2^-128 mod d: the inverse of 2^128 mod d by extended Euclid.
+        u32 two128 = powmod_host(2, 128, d);
+        i64 a = two128, m = d, x0 = 1, x1 = 0;
+        while (m) {
+            i64 q = a / m, t = a - q * m;
+            a = m; m = t;
+            t = x0 - q * x1; x0 = x1; x1 = t;
+        }
+        u32 rk = (u32)((x0 % (i64)d + d) % d);
+        c.rk[0] = rk;
+        for (int i = 1; i < 5; ++i) c.rk[i] = (u32)((u64)c.rk[i - 1] * c.rk[i - 1] % d);
+    } else {
+        for (int i = 0; i < 5; ++i) c.rk[i] = 0;
+    }
+    return c;
+}
+
+static DivTable make_div_table() {
+    DivTable t;
+    for (int k = 0; k < 32; ++k) {
+        u32 d1 = 1, d2 = 1;
+        if (k >= 1 && k < 16) d1 = (u32)((1ull << (2 * k)) - 1);
+        if (k >= 16) {
+            d1 = (u32)((1ull << k) - 1);
+            d2 = (u32)((1ull << k) + 1);
+        }
+        t.d[0][k] = make_div(d1);
+        t.d[1][k] = make_div(d2);
+    }
+    return t;
+}
+
+// Shifted emission of chunk c-1.  w0..w3: this lane's limbs of the chunk;
+// below: the limb under w0; a0, a1: the two limbs above w3.  sh < 0 shifts
+// right by -sh (< 64), sh >= 0 shifts left by sh (< 32).
+__device__ __forceinline__ void shift_window(const u32 w[4], u32 below, u32 a0, u32 a1, int sh,
+                                             u32 out[4]) {
+    const u32 x[7] = {below, w[0], w[1], w[2], w[3], a0, a1};  // x[i + 1] = limb i
+    if (sh < 0) {
+        const int R = -sh, qa = R >> 5, r = R & 31;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const u32 lo = qa ? x[j + 2] : x[j + 1];
+            const u32 hi = qa ? x[j + 3] : x[j + 2];
+            out[j] = fshr(lo, hi, (u32)r);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) out[j] = fshl(x[j], x[j + 1], (u32)sh);
+    }
+}
+
+// c_out = ((X - Z) >> R) / d1 / d2   (R < 64; d == 1 means no division)
+__device__ void chain_sub_shr_div(const u32* X, const u32* Z, u32* O, int Y, int R,
+                                  const DivConst& d1, const DivConst& d2) {
+    const int lane = lane_id();
+    const int nch = Y / CH;
+    u32 bw = 0, B1 = 0, B2 = 0;
+    u32 prev[4] = {0, 0, 0, 0};
+    for (int c = 0; c <= nch; ++c) {
+        u32 cur[4] = {0, 0, 0, 0};
+        if (c < nch) {
+            uint4 xv = ld4(X + c * CH + 4 * lane), zv = ld4(Z + c * CH + 4 * lane);
+            const u32 x[4] = {xv.x, xv.y, xv.z, xv.w}, z[4] = {zv.x, zv.y, zv.z, zv.w};
+            warp_sub_chunk(x, z, bw, cur);
+        }
+        if (c > 0) {
+            u32 a0 = __shfl_down_sync(FULL, prev[0], 1), a1 = __shfl_down_sync(FULL, prev[1], 1);
+            const u32 c0 = __shfl_sync(FULL, cur[0], 0), c1 = __shfl_sync(FULL, cur[1], 0);
+            if (lane == 31) { a0 = c0; a1 = c1; }
+            u32 v[4];
+            shift_window(prev, 0u, a0, a1, -R, v);
+            if (d1.d > 1) warp_exact_div_chunk(v, d1, B1);
+            if (d2.d > 1) warp_exact_div_chunk(v, d2, B2);
+            st4(O + (c - 1) * CH + 4 * lane, v);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) prev[j] = cur[j];
+    }
+}
+
+// c_out = X - (Z << S)   (S < 64)
+__device__ void chain_sub_shl(const u32* X, const u32* Z, u32* O, int Y, int S) {
+    const int lane = lane_id();
+    const int nch = Y / CH;
+    const int qa = S >> 5, s = S & 31;
+    u32 bw = 0, t2 = 0, t3 = 0;
+    for (int c = 0; c < nch; ++c) {
+        uint4 xv = ld4(X + c * CH + 4 * lane), zv = ld4(Z + c * CH + 4 * lane);
+        const u32 x[4] = {xv.x, xv.y, xv.z, xv.w};
+        u32 m1 = __shfl_up_sync(FULL, zv.w, 1), m2 = __shfl_up_sync(FULL, zv.z, 1);
+        if (lane == 0) { m1 = t3; m2 = t2; }
+        const u32 zw[6] = {m2, m1, zv.x, zv.y, zv.z, zv.w};  // zw[i + 2] = limb i
+        u32 sz[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const u32 hi = qa ? zw[j + 1] : zw[j + 2];
+            const u32 lo = qa ? zw[j] : zw[j + 1];
+            sz[j] = fshl(lo, hi, (u32)s);
+        }
+        u32 r[4];
+        warp_sub_chunk(x, sz, bw, r);
+        st4(O + c * CH + 4 * lane, r);
+        t3 = __shfl_sync(FULL, zv.w, 31);
+        t2 = __shfl_sync(FULL, zv.z, 31);
+    }
+}
+
+// Even-odd combine for node m >= 1 (eq. 4.5-4.6):
+//   A = W(x) + |W(-x)|, D = W(x) - |W(-x)|  (W(x) >= |W(-x)|)
+//   ye_m = (neg ? D : A) / 2,   yo_m = x (neg ? A : D) / 2,  x = 2^(m-1)
+__device__ void chain_even_odd(const u32* Pp, const u32* Mm, int len, bool neg, int m,
+                               u32* CE, u32* CO, int Y) {
+    const int lane = lane_id();
+    const int nch = Y / CH;
+    u32 cA = 0, bD = 0;
+    u32 pA[4] = {0, 0, 0, 0}, pD[4] = {0, 0, 0, 0};
+    u32 tA = 0, tD = 0;  // last limb of chunk c-2
+    const int sh_o = m == 1 ? -1 : m - 2;
+    for (int c = 0; c <= nch; ++c) {
+        u32 A[4] = {0, 0, 0, 0}, D[4] = {0, 0, 0, 0};
+        if (c < nch) {
+            u32 p[4], q[4];
+            ld4_masked(Pp, c * CH + 4 * lane, len, p);
+            ld4_masked(Mm, c * CH + 4 * lane, len, q);
+            warp_add_chunk(p, q, cA, A);
+            warp_sub_chunk(p, q, bD, D);
+        }
+        if (c > 0) {
+            // neighbours for both candidate values
+            u32 bA = __shfl_up_sync(FULL, pA[3], 1), bDv = __shfl_up_sync(FULL, pD[3], 1);
+            if (lane == 0) { bA = tA; bDv = tD; }
+            u32 aA0 = __shfl_down_sync(FULL, pA[0], 1), aA1 = __shfl_down_sync(FULL, pA[1], 1);
+            u32 aD0 = __shfl_down_sync(FULL, pD[0], 1), aD1 = __shfl_down_sync(FULL, pD[1], 1);
+            const u32 nA0 = __shfl_sync(FULL, A[0], 0), nA1 = __shfl_sync(FULL, A[1], 0);
+            const u32 nD0 = __shfl_sync(FULL, D[0], 0), nD1 = __shfl_sync(FULL, D[1], 0);
+            if (lane == 31) { aA0 = nA0; aA1 = nA1; aD0 = nD0; aD1 = nD1; }
+            u32 e_out[4], o_out[4];
+            if (neg) {
+                shift_window(pD, bDv, aD0, aD1, -1, e_out);
+                shift_window(pA, bA, aA0, aA1, sh_o, o_out);
+            } else {
+                shift_window(pA, bA, aA0, aA1, -1, e_out);
+                shift_window(pD, bDv, aD0, aD1, sh_o, o_out);
+            }
+            st4(CE + (c - 1) * CH + 4 * lane, e_out);
+            st4(CO + (c - 1) * CH + 4 * lane, o_out);
+        }
+        tA = __shfl_sync(FULL, pA[3], 31);
+        tD = __shfl_sync(FULL, pD[3], 31);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) { pA[j] = A[j]; pD[j] = D[j]; }
+    }
+}
+
+// Copy a row of `len` limbs into a value of Y limbs (zero-extended); zero if src == null.
+__device__ void chain_copy(const u32* src, int len, u32* dst, int Y) {
+    const int lane = lane_id();
+    for (int c = 0; c < Y; c += CH) {
+        u32 v[4] = {0, 0, 0, 0};
+        if (src) ld4_masked(src, c + 4 * lane, len, v);
+        st4(dst + c + 4 * lane, v);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Block-wide normalisation of non-negative column sums (recomposition).
+// ---------------------------------------------------------------------------
+struct BlockNormState {
+    u64 col_carry;  // carry of the previous chunk's last column
+    u32 carry;      // resolved 0/1 carry into this chunk
+};
+
+// cols: this thread's 4 column sums (each < 2^62).  sh: >= 2*warps+... words of shared scratch.
+__device__ void block_norm_unsigned(const u64 cols[4], BlockNormState& st, u32 out[4], u32* sh) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    u64* sh_c = reinterpret_cast<u64*>(sh);           // [blockDim] last-column carries
+    u32* sh_gp = sh + 2 * blockDim.x;                 // [nw] warp g/p bits, then [nw] warp carries
+    u32 d[4];
+    u64 c[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) { d[j] = (u32)cols[j]; c[j] = cols[j] >> 32; }
+    sh_c[tid] = c[3];
+    __syncthreads();
+    const u64 prev_c = tid == 0 ? st.col_carry : sh_c[tid - 1];
+    u64 y[4];
+    y[0] = (u64)d[0] + prev_c;
+#pragma unroll
+    for (int j = 1; j < 4; ++j) y[j] = (u64)d[j] + c[j - 1];
+    // per-limb generate (y >= 2^32) / propagate (y == 2^32 - 1), composed low to high
+    bool g = false, p = true;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const bool gj = y[j] >> 32, pj = y[j] == 0xffffffffull;
+        g = gj || (pj && g);
+        p = pj && p;
+    }
+    u32 wout;
+    warp_carry_scan(g, p, 0u, &wout);                 // warp aggregate with carry-in 0
+    const bool wp = __ballot_sync(FULL, p) == FULL;
+    if (lane == 0) sh_gp[warp] = (wout ? 1u : 0u) | (wp ? 2u : 0u);
+    const u64 last_c = sh_c[blockDim.x - 1];
+    __syncthreads();
+    if (warp == 0) {
+        // lanes past the last warp pass the carry through so lane 31 reports the block's carry
+        const u32 v = lane < nw ? sh_gp[lane] : 2u;
+        u32 bout;
+        const u32 cin = warp_carry_scan((v & 1u) != 0, (v & 2u) != 0, st.carry, &bout);
+        if (lane < nw) sh_gp[nw + lane] = cin;
+        if (lane == 0) sh_gp[2 * nw] = bout;
+    }
+    __syncthreads();
+    const u32 wcin = sh_gp[nw + warp];
+    u32 dummy;
+    u32 x = warp_carry_scan(g, p, wcin, &dummy);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const u64 v = y[j] + x;
+        out[j] = (u32)v;
+        x = (u32)(v >> 32);
+    }
+    const u32 new_carry = sh_gp[2 * nw];
+    __syncthreads();
+    st.carry = new_carry;
+    st.col_carry = last_c;
+}
+
+// out[0..out_len) = sum over terms t < nterms of term_t shifted by t * bstep limbs,
+// where term t has Y limbs and get(t, x) returns its limb x (0 <= x < Y).
+template <class Get>
+__device__ void block_recompose(Get get, long nterms, long Y, long bstep, u32* out, long out_len,
+                                u32* sh) {
+    BlockNormState st{0, 0};
+    const int tid = threadIdx.x;
+    const long chunk = 4L * blockDim.x;
+    const bool aligned = ((reinterpret_cast<uintptr_t>(out) & 15u) == 0);
+    for (long base = 0; base < out_len; base += chunk) {
+        u64 cols[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const long l = base + 4L * tid + j;
+            u64 S = 0;
+            if (l < out_len) {
+                long tlo = (l - Y) / bstep;  // first term that can reach limb l
+                if (tlo < 0) tlo = 0;
+                for (long t = tlo; t < nterms && t * bstep <= l; ++t) {
+                    const long x = l - t * bstep;
+                    if (x < Y) S += get(t, x);
+                }
+            }
+            cols[j] = S;
+        }
+        u32 d[4];
+        block_norm_unsigned(cols, st, d, sh);
+        const long pos = base + 4L * tid;
+        if (aligned && pos + 4 <= out_len) {
+            st4(out + pos, d);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (pos + j < out_len) out[pos + j] = d[j];
+        }
+    }
+}
+
+struct InterpArgs {
+    LevelGeom g;
+    const u32* y;
+    const uint8_t* su;
+    const uint8_t* sv;
+    u32* out;
+    long out_stride;
+    int out_len;
+    u32* work;        // global work base (per product 4 (n+1) Y limbs), null = shared
+    int use_smem;
+};
+
+__global__ void __launch_bounds__(1024)
+interp_kernel(InterpArgs a, DivTable dt, long P) {
+    extern __shared__ __align__(16) u32 sm[];
+    const long k = blockIdx.x;
+    if (k >= P) return;
+    const LevelGeom& g = a.g;
+    const int n = g.n, Y = g.Y;
+    const int npts = 2 * g.B - 1;
+    const int tid = threadIdx.x, warp = tid >> 5, nw = blockDim.x >> 5;
+
+    __shared__ int slot[2][33];
+    __shared__ __align__(16) u32 shscan[2 * 1024 + 80];
+    __shared__ const u32* terms[65];
+    u32* base = a.use_smem ? sm : a.work + k * (long)(4 * (n + 1)) * Y;
+    auto val = [&](int sl, int poly, int m) -> u32* {
+        return base + ((long)((sl * 2 + poly) * (n + 1) + m)) * Y;
+    };
+    const u32* yk = a.y + k * npts * (long)g.ystride;
+    auto sgn = [&](int p) -> bool {
+        bool s = false;
+        if (a.su) s ^= a.su[k * npts + p] != 0;
+        if (a.sv) s ^= a.sv[k * npts + p] != 0;
+        return s;
+    };
+    if (tid < 66) slot[tid / 33][tid % 33] = 0;
+    __syncthreads();
+
+    // ---- even-odd combine (chain 0: node 0) ----
+    for (int c = warp; c <= n; c += nw) {
+        if (c == 0) {
+            chain_copy(yk, 2 * g.e, val(0, 0, 0), Y);
+            chain_copy(nullptr, 0, val(0, 1, 0), Y);
+        } else {
+            const u32* Pp = yk + (2 * c - 1) * (long)g.ystride;
+            const u32* Mm = yk + (2 * c) * (long)g.ystride;
+            chain_even_odd(Pp, Mm, 2 * g.e, sgn(2 * c), c, val(0, 0, c), val(0, 1, c), Y);
+        }
+    }
+    __syncthreads();
+
+    // ---- Newton loop 1 (Theorem 3.2) ----
+    for (int kk = 1; kk <= n; ++kk) {
+        const int cnt = n - kk + 1;
+        for (int c = warp; c < 2 * cnt; c += nw) {
+            const int poly = c / cnt, m = kk + c % cnt;
+            const int sx = slot[poly][m], sz = slot[poly][m - 1];
+            const int R = m == kk ? 2 * (m - 1) : 2 * (m - kk - 1);
+            const bool div = m > kk;
+            chain_sub_shr_div(val(sx, poly, m), val(sz, poly, m - 1), val(1 - sx, poly, m), Y, R,
+                              div ? dt.d[0][kk] : dt.d[0][0], div ? dt.d[1][kk] : dt.d[1][0]);
+        }
+        __syncthreads();
+        if (tid < 2 * cnt) {
+            const int poly = tid / cnt, m = kk + tid % cnt;
+            slot[poly][m] ^= 1;
+        }
+        __syncthreads();
+    }
+
+    // ---- Newton loop 2 (Theorem 3.3) ----
+    for (int m = n - 1; m >= 1; --m) {
+        const int cnt = n - m;
+        for (int c = warp; c < 2 * cnt; c += nw) {
+            const int poly = c / cnt, kx = m + c % cnt;
+            const int sx = slot[poly][kx], sz = slot[poly][kx + 1];
+            chain_sub_shl(val(sx, poly, kx), val(sz, poly, kx + 1), val(1 - sx, poly, kx), Y,
+                          2 * (m - 1));
+        }
+        __syncthreads();
+        if (tid < 2 * cnt) {
+            const int poly = tid / cnt, kx = m + tid % cnt;
+            slot[poly][kx] ^= 1;
+        }
+        __syncthreads();
+    }
+
+    // ---- re-interleave and recompose: w_2i = ce_i, w_2i+1 = co_(i+1) ----
+    if (tid <= 2 * n) {
+        const int poly = tid & 1, m = (tid + 1) >> 1;
+        terms[tid] = val(slot[poly][m], poly, m);
+    }
+    __syncthreads();
+    block_recompose([&](long t, long x) -> u32 { return terms[t][x]; }, 2 * n + 1, Y, g.b,
+                    a.out + k * a.out_stride, a.out_len, shscan);
+}
+
+size_t interp_work_bytes(const LevelGeom& g) {
+    const size_t bytes = (size_t)4 * (g.n + 1) * g.Y * 4;
+    return bytes <= 160 * 1024 ? 0 : bytes;
+}
+
+cudaError_t launch_interp(const LevelGeom& g, const u32* y, const uint8_t* su, const uint8_t* sv,
+                          u32* out, long out_stride, int out_len, u32* work, long P,
+                          cudaStream_t st) {
+    if (P <= 0) return cudaSuccess;
+    static const DivTable dt = make_div_table();
+    InterpArgs a;
+    a.g = g;
+    a.y = y;
+    a.su = su;
+    a.sv = sv;
+    a.out = out;
+    a.out_stride = out_stride;
+    a.out_len = out_len;
+    const size_t wb = interp_work_bytes(g);
+    a.use_smem = wb == 0;
+    a.work = work;
+    if (!a.use_smem && !work) return cudaErrorInvalidValue;
+    const size_t smem = a.use_smem ? (size_t)4 * (g.n + 1) * g.Y * 4 : 0;
+    int warps = 2 * g.n;
+    if (warps < 4) warps = 4;
+    if (warps > 32) warps = 32;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(interp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+        attr_set = true;
+    }
+    interp_kernel<<<(unsigned)P, warps * 32, smem, st>>>(a, dt, P);
+    return cudaGetLastError();
+}
+
+// ===========================================================================
+// Overlap-add of equally spaced rows (sliced unbalanced products).
+// ===========================================================================
+__global__ void __launch_bounds__(1024)
+overlap_add_kernel(const u32* rows, long row_stride, int row_len, long count, long off, u32* out,
+                   long out_len) {
+    __shared__ __align__(16) u32 shscan[2 * 1024 + 80];
+    block_recompose([&](long t, long x) -> u32 { return rows[t * row_stride + x]; }, count,
+                    row_len, off, out, out_len, shscan);
+}
+
+cudaError_t launch_overlap_add(const u32* rows, long row_stride, int row_len, long count, long off,
+                               u32* out, long out_len, cudaStream_t st) {
+    if (count <= 0) return cudaErrorInvalidValue;
+    overlap_add_kernel<<<1, 1024, 0, st>>>(rows, row_stride, row_len, count, off, out, out_len);
+    return cudaGetLastError();
+}
+
+__global__ void zero_kernel(u32* p, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x)
+        p[i] = 0;
+}
+
+cudaError_t launch_zero(u32* p, size_t n, cudaStream_t st) {
+    if (!n) return cudaSuccess;
+    size_t blocks = (n + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    zero_kernel<<<(unsigned)blocks, 256, 0, st>>>(p, n);
+    return cudaGetLastError();
+}
+
+}  // namespace tc

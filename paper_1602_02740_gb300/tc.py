@@ -1,0 +1,353 @@
+"""Thin ctypes binding of ``libtc.so`` (include/tc.h), same names as the C ABI.
+
+Only argument marshalling happens here: torch tensors supply device memory
+and streams, every arithmetic step runs in the library's CUDA kernels.  Limb
+tensors are ``torch.int32`` holding uint32 bit patterns (or ``torch.uint32``).
+The library is loaded from this package directory on first use; if it is
+missing the call raises ``RuntimeError`` (there is no fallback path).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtc.so")
+
+TC_OK, TC_EINVAL, TC_ENOMEM, TC_EBUSY, TC_ETIMEOUT, TC_EDEVICE, TC_EPENDING = 0, -1, -2, -3, -4, -5, 1
+TC_MAX_LEVELS = 8
+
+_lock = threading.Lock()
+_lib = None
+
+
+class TCError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = lib().tc_strerror(status).decode()
+        cuda = lib().tc_last_cuda_error()
+        super().__init__(f"{where}: {msg} (status {status}, cuda error {cuda})")
+
+
+class tc_opts(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int), ("B", ctypes.c_int * TC_MAX_LEVELS)]
+
+    @classmethod
+    def of(cls, Bs: Sequence[int]) -> "tc_opts":
+        o = cls()
+        o.levels = len(Bs)
+        for i, B in enumerate(Bs):
+            o.B[i] = int(B)
+        return o
+
+    def plan(self):
+        return [self.B[i] for i in range(self.levels)]
+
+
+_vp, _sz, _u32p, _i64p, _u8p = (ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
+                                ctypes.c_void_p, ctypes.c_void_p)
+_optp = ctypes.POINTER(tc_opts)
+
+_SIGS = {
+    "tc_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, _sz, ctypes.c_char_p]),
+    "tc_destroy": (None, [_vp]),
+    "tc_plan_for": (ctypes.c_int, [_vp, _sz, _optp]),
+    "tc_scratch_bytes": (ctypes.c_int, [_vp, _sz, _sz, _optp, ctypes.POINTER(ctypes.c_size_t)]),
+    "tc_mul": (ctypes.c_int, [_vp, _u32p, _sz, _u32p, _sz, _u32p, _optp, _vp]),
+    "tc_sqr": (ctypes.c_int, [_vp, _u32p, _sz, _u32p, _optp, _vp]),
+    "tc_mul_batch": (ctypes.c_int, [_vp, _sz, _u32p, _i64p, _i64p, _u32p, _i64p, _i64p, _u32p,
+                                    _i64p, _optp, _vp]),
+    "tc_mul_uniform": (ctypes.c_int, [_vp, _sz, _sz, _u32p, _sz, _u32p, _sz, _u32p, _sz, _optp, _vp]),
+    "tc_mul_uniform_host": (ctypes.c_int, [_vp, _sz, _sz, _u32p, _u32p, _u32p, _optp, _vp]),
+    "tc_schoolbook": (ctypes.c_int, [_sz, _sz, _u32p, _sz, _u32p, _sz, _u32p, _sz, _vp]),
+    "tc_toom_evaluate": (ctypes.c_int, [_sz, _sz, ctypes.c_int, _u32p, _sz, _u32p, _sz, _u8p, _vp]),
+    "tc_toom_interpolate": (ctypes.c_int, [_sz, _sz, ctypes.c_int, _u32p, _sz, _u8p, _u8p, _u32p,
+                                           _sz, _vp, _vp]),
+    "tc_toom_interpolate_work_bytes": (ctypes.c_size_t, [_sz, ctypes.c_int]),
+    "tc_serve_submit": (ctypes.c_int, [_vp, _u32p, _sz, _u32p, _sz, _u32p,
+                                       ctypes.POINTER(ctypes.c_uint64)]),
+    "tc_serve_poll": (ctypes.c_int, [_vp, ctypes.c_uint64]),
+    "tc_serve_stats": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_uint64)]),
+    "tc_serve_stop": (ctypes.c_int, [_vp]),
+    "tc_profile_enable": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "tc_profile_read": (ctypes.c_int, [_vp, ctypes.c_void_p, ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_int)]),
+    "tc_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "tc_last_cuda_error": (ctypes.c_int, []),
+}
+
+EXPORTED = tuple(_SIGS)
+
+
+def lib():
+    """Load libtc.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                                   "`python -m paper_1602_02740_gb300.build`")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in _SIGS.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(status: int, where: str):
+    if status != TC_OK:
+        raise TCError(status, where)
+
+
+def _ptr(t) -> int:
+    """Device (or host) address of a tensor / numpy array."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+def _stream(stream) -> Optional[int]:
+    import torch
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _opts(plan):
+    if plan is None:
+        return None
+    o = plan if isinstance(plan, tc_opts) else tc_opts.of(plan)
+    return ctypes.byref(o)
+
+
+class Context:
+    """Owns a tc_ctx (scratch arena, plan table, serving loop)."""
+
+    def __init__(self, device: int = 0, budget_bytes: int = 0, table: Optional[str] = None):
+        h = ctypes.c_void_p()
+        _check(lib().tc_create(ctypes.byref(h), device, budget_bytes,
+                               table.encode() if table else None), "tc_create")
+        self.handle = h.value
+        self.device = device
+
+    def close(self):
+        if self.handle:
+            lib().tc_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def tc_create(device: int = 0, budget_bytes: int = 0, table: Optional[str] = None) -> Context:
+    return Context(device, budget_bytes, table)
+
+
+def tc_destroy(ctx: Context):
+    ctx.close()
+
+
+def tc_plan_for(ctx: Context, limbs: int):
+    o = tc_opts()
+    _check(lib().tc_plan_for(ctx.handle, limbs, ctypes.byref(o)), "tc_plan_for")
+    return o.plan()
+
+
+def tc_scratch_bytes(ctx: Context, count: int, limbs: int, plan=None) -> int:
+    v = ctypes.c_size_t()
+    _check(lib().tc_scratch_bytes(ctx.handle, count, limbs, _opts(plan), ctypes.byref(v)),
+           "tc_scratch_bytes")
+    return v.value
+
+
+def _empty(n, device):
+    import torch
+    return torch.empty(n, dtype=torch.int32, device=device)
+
+
+def tc_mul(ctx: Context, a, b, out=None, plan=None, stream=None):
+    """out = a * b (1-D int32 device tensors of limbs); returns out (len(a)+len(b) limbs)."""
+    na, nb = a.numel(), b.numel()
+    if out is None:
+        out = _empty(na + nb, a.device)
+    assert out.numel() == na + nb
+    _check(lib().tc_mul(ctx.handle, _ptr(a), na, _ptr(b), nb, _ptr(out), _opts(plan),
+                        _stream(stream)), "tc_mul")
+    return out
+
+
+def tc_sqr(ctx: Context, a, out=None, plan=None, stream=None):
+    na = a.numel()
+    if out is None:
+        out = _empty(2 * na, a.device)
+    _check(lib().tc_sqr(ctx.handle, _ptr(a), na, _ptr(out), _opts(plan), _stream(stream)), "tc_sqr")
+    return out
+
+
+def tc_mul_uniform(ctx: Context, A, B, OUT=None, plan=None, stream=None):
+    """Row-wise products of 2-D (count, L) int32 device tensors; OUT is (count, 2L)."""
+    count, L = A.shape
+    if OUT is None:
+        import torch
+        OUT = torch.empty((count, 2 * L), dtype=torch.int32, device=A.device)
+    _check(lib().tc_mul_uniform(ctx.handle, count, L, _ptr(A), A.stride(0), _ptr(B), B.stride(0),
+                                _ptr(OUT), OUT.stride(0), _opts(plan), _stream(stream)),
+           "tc_mul_uniform")
+    return OUT
+
+
+def tc_mul_uniform_host(ctx: Context, A, B, OUT, plan=None, stream=None):
+    """Host-memory variant: A, B (count, L) and OUT (count, 2L) are CPU tensors/arrays."""
+    count, L = A.shape
+    _check(lib().tc_mul_uniform_host(ctx.handle, count, L, _ptr(A), _ptr(B), _ptr(OUT),
+                                     _opts(plan), _stream(stream)), "tc_mul_uniform_host")
+    return OUT
+
+
+def tc_mul_batch(ctx: Context, A, a_off, a_len, B, b_off, b_len, OUT, out_off, plan=None,
+                 stream=None):
+    """Packed batch; offsets/lengths are host int64 numpy arrays."""
+    arrs = [np.ascontiguousarray(x, dtype=np.int64) for x in (a_off, a_len, b_off, b_len, out_off)]
+    count = len(arrs[0])
+    _check(lib().tc_mul_batch(ctx.handle, count, _ptr(A), arrs[0].ctypes.data, arrs[1].ctypes.data,
+                              _ptr(B), arrs[2].ctypes.data, arrs[3].ctypes.data, _ptr(OUT),
+                              arrs[4].ctypes.data, _opts(plan), _stream(stream)), "tc_mul_batch")
+    return OUT
+
+
+def tc_schoolbook(A, B, OUT=None, stream=None):
+    count, L = A.shape
+    if OUT is None:
+        import torch
+        OUT = torch.empty((count, 2 * L), dtype=torch.int32, device=A.device)
+    _check(lib().tc_schoolbook(count, L, _ptr(A), A.stride(0), _ptr(B), B.stride(0), _ptr(OUT),
+                               OUT.stride(0), _stream(stream)), "tc_schoolbook")
+    return OUT
+
+
+def level_sizes(limbs: int, B: int):
+    """(b, e, estride, ystride) of one level, as the library lays it out."""
+    n = B - 1
+    b = -(-limbs // B)
+    e = b + -(-(n * (n - 1) + 1) // 32)
+    return b, e, -(-e // 4) * 4, -(-2 * e // 4) * 4
+
+
+def tc_toom_evaluate(U, B: int, OUT=None, SGN=None, stream=None):
+    """Evaluate rows of U (count, L) at the 2B-1 points; returns (OUT, SGN)."""
+    import torch
+    count, L = U.shape
+    _, e, estride, _ = level_sizes(L, B)
+    if OUT is None:
+        OUT = torch.empty((count, 2 * B - 1, estride), dtype=torch.int32, device=U.device)
+    if SGN is None:
+        SGN = torch.empty((count, 2 * B - 1), dtype=torch.uint8, device=U.device)
+    _check(lib().tc_toom_evaluate(count, L, B, _ptr(U), U.stride(0), _ptr(OUT), OUT.shape[-1],
+                                  _ptr(SGN), _stream(stream)), "tc_toom_evaluate")
+    return OUT, SGN
+
+
+def tc_toom_interpolate_work_bytes(limbs: int, B: int) -> int:
+    return lib().tc_toom_interpolate_work_bytes(limbs, B)
+
+
+def tc_toom_interpolate(Y, limbs: int, B: int, SGN_U=None, SGN_V=None, OUT=None, work=None,
+                        stream=None):
+    """Y: (count, 2B-1, ystride) products; returns OUT (count, 2*limbs)."""
+    import torch
+    count = Y.shape[0]
+    if OUT is None:
+        OUT = torch.empty((count, 2 * limbs), dtype=torch.int32, device=Y.device)
+    wb = tc_toom_interpolate_work_bytes(limbs, B)
+    if wb and work is None:
+        work = torch.empty(wb * count, dtype=torch.uint8, device=Y.device)
+    _check(lib().tc_toom_interpolate(count, limbs, B, _ptr(Y), Y.shape[-1], _ptr(SGN_U), _ptr(SGN_V),
+                                     _ptr(OUT), OUT.stride(0), _ptr(work) if wb else None,
+                                     _stream(stream)), "tc_toom_interpolate")
+    return OUT
+
+
+def tc_serve_submit(ctx: Context, a, b, out) -> int:
+    t = ctypes.c_uint64()
+    st = lib().tc_serve_submit(ctx.handle, _ptr(a), a.numel(), _ptr(b), b.numel(), _ptr(out),
+                               ctypes.byref(t))
+    if st == TC_EBUSY:
+        return -1
+    _check(st, "tc_serve_submit")
+    return t.value
+
+
+def tc_serve_poll(ctx: Context, ticket: int) -> bool:
+    st = lib().tc_serve_poll(ctx.handle, ticket)
+    if st == TC_EPENDING:
+        return False
+    _check(st, "tc_serve_poll")
+    return True
+
+
+def tc_serve_stats(ctx: Context):
+    p50, p99, bps = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    n = ctypes.c_uint64()
+    _check(lib().tc_serve_stats(ctx.handle, ctypes.byref(p50), ctypes.byref(p99),
+                                ctypes.byref(bps), ctypes.byref(n)), "tc_serve_stats")
+    return {"p50_ms": p50.value, "p99_ms": p99.value, "bits_per_s": bps.value,
+            "completed": n.value}
+
+
+def tc_serve_stop(ctx: Context):
+    _check(lib().tc_serve_stop(ctx.handle), "tc_serve_stop")
+
+
+class tc_phase_stat(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("level", ctypes.c_int), ("launches", ctypes.c_int),
+                ("ms", ctypes.c_double), ("bytes", ctypes.c_double),
+                ("limb_products", ctypes.c_double)]
+
+
+PHASE_NAMES = {0: "evaluate", 1: "base_case", 2: "interpolate"}
+
+
+def tc_profile_enable(ctx: Context, on: bool = True):
+    _check(lib().tc_profile_enable(ctx.handle, 1 if on else 0), "tc_profile_enable")
+
+
+def tc_profile_read(ctx: Context):
+    """List of dicts: kind, level, launches, ms, bytes, limb_products."""
+    arr = (tc_phase_stat * 64)()
+    n = ctypes.c_int()
+    _check(lib().tc_profile_read(ctx.handle, arr, 64, ctypes.byref(n)), "tc_profile_read")
+    return [{"kind": PHASE_NAMES[a.kind], "level": a.level, "launches": a.launches, "ms": a.ms,
+             "bytes": a.bytes, "limb_products": a.limb_products} for a in arr[:n.value]]
+
+
+# ---- limb helpers (numpy uint32 <-> torch int32) ----
+
+def to_device(x: np.ndarray, device="cuda"):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.uint32).view(np.int32)).to(device)
+
+
+def to_numpy(t) -> np.ndarray:
+    return t.detach().cpu().numpy().view(np.uint32)

@@ -26,4 +26,5 @@ def tc():
     if not cuda_available():
         pytest.skip("no CUDA device")
     import paper_1602_02740_gb300 as lib
+    from paper_1602_02740_gb300 import tc as _binding  # noqa: F401  (loads the submodule)
     return lib

@@ -1,0 +1,217 @@
+"""GPU parity: every step and the whole product, limb-exact against the oracle.
+
+All arithmetic is exact integer, so the bar is bit-exactness everywhere.
+"""
+import numpy as np
+import pytest
+
+from oracle import native, residues, toom
+from oracle.limbs import from_int, to_int
+from paper_1602_02740_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def same_limbs(got, want_int_or_arr, L=None):
+    """Bit-exact comparison with a readable failure (first differing limb)."""
+    want = want_int_or_arr
+    if not isinstance(want, np.ndarray):
+        want = from_int(int(want), len(got))
+    got = np.asarray(got, dtype=np.uint32)
+    if len(got) != len(want) or not np.array_equal(got, want):
+        bad = np.nonzero(got != want)[0] if len(got) == len(want) else [-1]
+        i = int(bad[0])
+        raise AssertionError(f"{len(bad)} limbs differ; first at {i}: got "
+                             f"{hex(int(got[i])) if i >= 0 else len(got)} want "
+                             f"{hex(int(want[i])) if i >= 0 else len(want)}")
+    return True
+
+
+def dev(x):
+    from paper_1602_02740_gb300 import tc
+    return tc.to_device(x)
+
+
+def host(t):
+    from paper_1602_02740_gb300 import tc
+    return tc.to_numpy(t)
+
+
+@pytest.fixture(scope="module")
+def ctx(tc):
+    c = tc.tc.tc_create(0)
+    yield c
+    c.close()
+
+
+# ---------------------------------------------------------------- schoolbook
+
+@pytest.mark.parametrize("L", [1, 2, 3, 4, 5, 7, 8, 15, 16, 17, 31, 33, 48, 49, 64, 65, 66, 100,
+                               127, 128, 129, 255, 256, 257, 300, 511, 512, 513, 777, 1024])
+def test_schoolbook_vs_oracle(tc, L):
+    count = 3
+    A = np.stack([inputs.uniform(L, 10 * L + k) for k in range(count - 1)] + [inputs.all_ones(L)])
+    B = np.stack([inputs.uniform(L, 7 * L + k) for k in range(count - 1)] + [inputs.all_ones(L)])
+    out = host(tc.tc.tc_schoolbook(dev(A), dev(B)))
+    for k in range(count):
+        assert np.array_equal(out[k], native.schoolbook(A[k], B[k])), (L, k)
+
+
+def test_schoolbook_many_and_strided(tc):
+    import torch
+    L, count = 70, 1000
+    A = np.stack([inputs.uniform(L, k) for k in range(count)])
+    B = np.stack([inputs.sparse(L, 5000 + k) for k in range(count)])
+    dA = dev(np.pad(A, ((0, 0), (0, 5))))[:, :L]   # row stride 75
+    dB = dev(B)
+    out = host(tc.tc.tc_schoolbook(dA, dB))
+    for k in range(0, count, 37):
+        assert np.array_equal(out[k], native.schoolbook(A[k], B[k]))
+
+
+# ---------------------------------------------------------------- evaluation
+
+EVAL_CASES = [(2, 1), (2, 5), (3, 7), (3, 1024), (4, 9), (5, 33), (8, 100), (8, 129),
+              (16, 16), (16, 300), (16, 2055), (32, 32), (32, 999)]
+
+
+@pytest.mark.parametrize("B,L", EVAL_CASES)
+@pytest.mark.parametrize("kind", ["uniform", "all_ones", "sparse"])
+def test_evaluate_vs_oracle(tc, B, L, kind):
+    count = 2
+    U = np.stack([inputs.operand(kind, L, 100 * B + L + k) for k in range(count)])
+    OUT, SGN = tc.tc.tc_toom_evaluate(dev(U), B)
+    out, sgn = host(OUT), SGN.cpu().numpy()
+    b = toom.ceil_div(L, B)
+    e = b + toom.growth_limbs(B)
+    for k in range(count):
+        vals = toom.evaluate(toom.split(to_int(U[k]), B, b))
+        for p, v in enumerate(vals):
+            assert to_int(out[k, p]) == abs(v), (B, L, kind, k, p)
+            assert int(sgn[k, p]) == (1 if v < 0 else 0), (B, L, kind, k, p)
+            assert not out[k, p, e:].any()
+
+
+def test_evaluate_equal_halves_sign(tc):
+    # u_0 = u_1 makes U(-1) = 0 exactly; E = O on every limb (full-length sign scan)
+    L = 4000
+    h = inputs.uniform(L // 2, 3)
+    U = np.concatenate([h, h])[None, :]
+    OUT, SGN = tc.tc.tc_toom_evaluate(dev(U), 2)
+    out = host(OUT)
+    assert not out[0, 2].any() and int(SGN.cpu()[0, 2]) == 0
+    assert to_int(out[0, 1]) == 2 * to_int(h)
+
+
+# ---------------------------------------------------------------- interpolation
+
+def _oracle_level(u, v, L, B):
+    b = toom.ceil_div(L, B)
+    ue = toom.evaluate(toom.split(u, B, b))
+    ve = toom.evaluate(toom.split(v, B, b))
+    y = [p * q for p, q in zip(ue, ve)]
+    return y
+
+
+INTERP_CASES = [(2, 4), (2, 1000), (3, 9), (3, 1024), (4, 100), (5, 77), (8, 515), (16, 64),
+                (16, 2055), (16, 32768), (32, 96), (32, 4000), (8, 40000)]
+
+
+@pytest.mark.parametrize("B,L", INTERP_CASES)
+@pytest.mark.parametrize("kind", ["uniform", "all_ones"])
+def test_interpolate_vs_oracle(tc, B, L, kind):
+    import torch
+    count = 2
+    _, e, _, ystride = tc.tc.level_sizes(L, B)
+    Y = np.zeros((count, 2 * B - 1, ystride), dtype=np.uint32)
+    S = np.zeros((count, 2 * B - 1), dtype=np.uint8)
+    want = []
+    for k in range(count):
+        a = inputs.operand(kind, L, 31 * L + k)
+        b = inputs.operand(kind, L, 17 * L + k + 1)
+        y = _oracle_level(to_int(a), to_int(b), L, B)
+        for p, val in enumerate(y):
+            Y[k, p, :2 * e] = from_int(abs(val), 2 * e)
+            S[k, p] = 1 if val < 0 else 0
+        want.append(to_int(a) * to_int(b))
+    out = host(tc.tc.tc_toom_interpolate(dev(Y), L, B, SGN_U=torch.from_numpy(S).cuda()))
+    for k in range(count):
+        assert same_limbs(out[k], want[k]), (B, L, kind, k)
+
+
+# ---------------------------------------------------------------- whole product
+
+MUL_CASES = [
+    (1, None), (2, None), (5, None), (64, None), (128, None), (129, None), (1024, [3]),
+    (1024, None), (1000, [2, 2, 2]), (3000, [16]), (3000, [4, 4]), (5000, [32]),
+    (2055, [8, 4]), (32768, None), (32768, [16, 8, 4]), (32768, [2, 2, 2, 2, 2, 2, 2, 2]),
+]
+
+
+@pytest.mark.parametrize("L,plan", MUL_CASES)
+@pytest.mark.parametrize("kind", ["uniform", "all_ones", "sparse"])
+def test_mul_vs_oracle(ctx, tc, L, plan, kind):
+    a = inputs.operand(kind, L, L + 1)
+    b = inputs.operand(kind, L, L + 2)
+    out = host(tc.tc.tc_mul(ctx, dev(a), dev(b), plan=plan))
+    want = native.schoolbook(a, b) if L <= 4096 else from_int(to_int(a) * to_int(b), 2 * L)
+    assert same_limbs(out, want)
+
+
+@pytest.mark.parametrize("L,plan", [(1, None), (100, None), (1024, [3]), (4096, [16]), (10000, None)])
+def test_square_vs_oracle(ctx, tc, L, plan):
+    a = inputs.uniform(L, 99 + L)
+    da = dev(a)
+    out = host(tc.tc.tc_mul(ctx, da, da, plan=plan))
+    assert same_limbs(out, to_int(a) ** 2)
+    out2 = host(tc.tc.tc_sqr(ctx, da, plan=plan))
+    assert np.array_equal(out, out2)
+
+
+@pytest.mark.parametrize("na,nb", [(1, 7), (7, 1), (100, 150), (150, 100), (300, 1200),
+                                   (5000, 1234), (64, 65536), (1, 1), (3, 0), (0, 5)])
+def test_unbalanced_and_empty(ctx, tc, na, nb):
+    import torch
+    a = inputs.uniform(na, 1) if na else np.zeros(0, np.uint32)
+    b = inputs.uniform(nb, 2) if nb else np.zeros(0, np.uint32)
+    da = dev(a) if na else torch.empty(0, dtype=torch.int32, device="cuda")
+    db = dev(b) if nb else torch.empty(0, dtype=torch.int32, device="cuda")
+    out = host(tc.tc.tc_mul(ctx, da, db))
+    assert len(out) == na + nb
+    assert same_limbs(out, to_int(a) * to_int(b))
+
+
+def test_uniform_batch_matches_single(ctx, tc):
+    L, count = 4096, 12
+    A = np.stack([inputs.uniform(L, k) for k in range(count)])
+    B = np.stack([inputs.uniform(L, 100 + k) for k in range(count)])
+    OUT = host(tc.tc.tc_mul_uniform(ctx, dev(A), dev(B)))
+    for k in range(count):
+        single = host(tc.tc.tc_mul(ctx, dev(A[k]), dev(B[k])))
+        assert np.array_equal(OUT[k], single)
+        assert same_limbs(OUT[k], to_int(A[k]) * to_int(B[k]))
+
+
+def test_host_entry_point(ctx, tc):
+    import torch
+    L, count = 3000, 5
+    A = np.stack([inputs.uniform(L, k) for k in range(count)])
+    B = np.stack([inputs.uniform(L, 50 + k) for k in range(count)])
+    OUT = np.zeros((count, 2 * L), dtype=np.uint32)
+    tc.tc.tc_mul_uniform_host(ctx, A, B, OUT)
+    for k in range(count):
+        assert same_limbs(OUT[k], to_int(A[k]) * to_int(B[k]))
+
+
+def test_batch_mixed_sizes(ctx, tc):
+    la, lb = inputs.batch_lengths(120, seed=4, lo=64, hi=6000)
+    a_off = np.concatenate([[0], np.cumsum(la)[:-1]])
+    b_off = np.concatenate([[0], np.cumsum(lb)[:-1]])
+    o_off = np.concatenate([[0], np.cumsum(la + lb)[:-1]])
+    A = inputs.uniform(int(la.sum()), 1)
+    B = inputs.uniform(int(lb.sum()), 2)
+    import torch
+    OUT = torch.zeros(int((la + lb).sum()), dtype=torch.int32, device="cuda")
+    tc.tc.tc_mul_batch(ctx, dev(A), a_off, la, dev(B), b_off, lb, OUT, o_off)
+    want = native.schoolbook_batch(A, a_off, la, B, b_off, lb, o_off, int((la + lb).sum()))
+    assert np.array_equal(host(OUT), want)
