@@ -146,9 +146,128 @@ leaf_kernel(const u32* __restrict__ A, long lda, const u32* __restrict__ Bm, lon
     }
 }
 
+// ---------------------------------------------------------------------------
+// Lane-per-product schoolbook for large batches.
+//
+// A warp holds 32 independent products, one per lane, so all lanes follow the
+// same schedule.  A lane walks the 8x8 tiles (I, J) of its product one
+// anti-diagonal D = I + J at a time; tile products land in columns
+// 8D .. 8D+14, kept as fifteen 96-bit Comba accumulators in registers.  Once
+// anti-diagonal D is done, columns 8D .. 8D+7 are final: the lane folds them
+// into a running 64-bit carry, writes eight result limbs and slides the
+// window by eight columns.  Operand slices come straight from global memory
+// as 32-byte vectors (L1-resident: a warp touches 32 x 2s limbs).
+//
+// Squaring (a == b) accumulates only the products a_i a_j with i < j and
+// doubles them at emission, adding the squares a_i^2 on the even columns.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void load8(const u32* row, int pos, int s, bool vec, u32 v[8]) {
+    if (vec && pos + 8 <= s) {
+        const uint4 x = *reinterpret_cast<const uint4*>(row + pos);
+        const uint4 y = *reinterpret_cast<const uint4*>(row + pos + 4);
+        v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+        v[4] = y.x; v[5] = y.y; v[6] = y.z; v[7] = y.w;
+    } else {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = (pos + k < s) ? row[pos + k] : 0u;
+    }
+}
+
+template <bool SQ>
+__global__ void __launch_bounds__(128)
+leaf_lane_kernel(const u32* __restrict__ A, long lda, const u32* __restrict__ Bm, long ldb,
+                 u32* __restrict__ OUT, long ldo, int s, long P, int vec) {
+    const long p0 = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = p0 < P;
+    const long p = active ? p0 : P - 1;
+    const u32* a = A + p * lda;
+    const u32* b = SQ ? a : Bm + p * ldb;
+    u32* out = OUT + p * ldo;
+    const int T = (s + 7) / 8;
+    const int out_len = 2 * s;
+    u32 lo[15], mid[15], hi[15];
+#pragma unroll
+    for (int k = 0; k < 15; ++k) { lo[k] = 0; mid[k] = 0; hi[k] = 0; }
+    u64 carry = 0;
+    for (int D = 0; D <= 2 * T - 2; ++D) {
+        const int Ilo = D - T + 1 > 0 ? D - T + 1 : 0;
+        const int Ihi = D < T - 1 ? D : T - 1;
+        for (int I = Ilo; I <= Ihi; ++I) {
+            const int J = D - I;
+            if (SQ && I > J) break;
+            u32 a8[8], b8[8];
+            load8(a, 8 * I, s, vec, a8);
+            load8(b, 8 * J, s, vec, b8);
+            if (SQ && I == J) {
+#pragma unroll
+                for (int r = 0; r < 8; ++r)
+#pragma unroll
+                    for (int c = r + 1; c < 8; ++c) mac96(lo[r + c], mid[r + c], hi[r + c], a8[r], b8[c]);
+            } else {
+#pragma unroll
+                for (int r = 0; r < 8; ++r)
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) mac96(lo[r + c], mid[r + c], hi[r + c], a8[r], b8[c]);
+            }
+        }
+        // columns 8D .. 8D+7 are complete (8D .. 8D+14 when D is the last)
+        const bool last = D == 2 * T - 2;
+        u32 sq8[8];
+        if (SQ) load8(a, 4 * D, s, false, sq8);  // a_(4D + k/2) for the even columns
+#pragma unroll
+        for (int k = 0; k < 15; ++k) {
+            if (k >= 8 && !last) break;
+            u64 vlo = lo[k], vmid = mid[k], vhi = hi[k];
+            if (SQ) {
+                // 2 (lo + mid 2^32 + hi 2^64) + a_(c/2)^2 on even columns c = 8D + k
+                vhi = (vhi << 1) | (vmid >> 31);
+                vmid = ((vmid << 1) & 0xffffffffull) | (vlo >> 31);
+                vlo = (vlo << 1) & 0xffffffffull;
+                if ((k & 1) == 0) {
+                    const int i = 4 * D + k / 2;
+                    u32 x = 0;
+                    if (k < 8) x = sq8[k / 2];
+                    else if (i < s) x = a[i];
+                    const u64 sqv = (u64)x * x;
+                    vlo += sqv & 0xffffffffull;
+                    vmid += sqv >> 32;
+                }
+            }
+            const u64 t = vlo + (carry & 0xffffffffull);
+            const int c = 8 * D + k;
+            if (active && c < out_len) out[c] = (u32)t;
+            carry = (carry >> 32) + (t >> 32) + vmid + (vhi << 32);
+        }
+        if (last) {
+            const int c = 8 * D + 15;
+            if (active && c < out_len) out[c] = (u32)carry;
+        }
+#pragma unroll
+        for (int k = 0; k < 15; ++k) {
+            lo[k] = k + 8 < 15 ? lo[k + 8] : 0u;
+            mid[k] = k + 8 < 15 ? mid[k + 8] : 0u;
+            hi[k] = k + 8 < 15 ? hi[k + 8] : 0u;
+        }
+    }
+}
+
+// Products at or above this count use the lane-per-product kernel.
+constexpr long LANE_KERNEL_MIN = 4096;
+
 cudaError_t launch_leaf(const u32* A, long lda, const u32* Bm, long ldb, u32* OUT, long ldo,
                         int s, long P, cudaStream_t st) {
     if (P <= 0) return cudaSuccess;
+    const bool square = (A == Bm && lda == ldb);
+    if (P >= LANE_KERNEL_MIN) {
+        const bool vec = ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(Bm)) & 15u) == 0 &&
+                         lda % 4 == 0 && ldb % 4 == 0;
+        const unsigned grid = (unsigned)((P + 127) / 128);
+        if (square)
+            leaf_lane_kernel<true><<<grid, 128, 0, st>>>(A, lda, Bm, ldb, OUT, ldo, s, P, vec);
+        else
+            leaf_lane_kernel<false><<<grid, 128, 0, st>>>(A, lda, Bm, ldb, OUT, ldo, s, P, vec);
+        return cudaGetLastError();
+    }
     LeafGeom g = leaf_geom(s);
     const int tiles = g.RB * g.CT;
     const size_t smem_max = 220 * 1024;

@@ -427,11 +427,13 @@ __device__ void block_recompose(Get get, long nterms, long Y, long bstep, u32* o
             const long l = base + 4L * tid + j;
             u64 S = 0;
             if (l < out_len) {
-                long tlo = (l - Y) / bstep;  // first term that can reach limb l
-                if (tlo < 0) tlo = 0;
-                for (long t = tlo; t < nterms && t * bstep <= l; ++t) {
+                // terms t with 0 <= l - t*bstep < Y, scanned down from the last one reaching l
+                long t = l / bstep;
+                if (t > nterms - 1) t = nterms - 1;
+                for (; t >= 0; --t) {
                     const long x = l - t * bstep;
-                    if (x < Y) S += get(t, x);
+                    if (x >= Y) break;
+                    S += get(t, x);
                 }
             }
             cols[j] = S;
@@ -547,6 +549,92 @@ interp_kernel(InterpArgs a, DivTable dt, long P) {
                     a.out + k * a.out_stride, a.out_len, shscan);
 }
 
+// ---------------------------------------------------------------------------
+// Warp-per-product interpolation for small values (many products per level).
+// One warp runs every chain of one product in sequence, so the paper's in-place
+// orders apply directly: loop 1 visits m from n down to k (each update reads the
+// old c[m-1]); loop 2 visits k upward (each update reads the old c[k+1]).  One
+// value slot per (polynomial, node); no block barriers.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+interp_warp_kernel(InterpArgs a, DivTable dt, long P) {
+    extern __shared__ __align__(16) u32 sm[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wpb = blockDim.x >> 5;
+    const long k = (long)blockIdx.x * wpb + warp;
+    if (k >= P) return;  // warp-uniform
+    const LevelGeom& g = a.g;
+    const int n = g.n, Y = g.Y;
+    const int npts = 2 * g.B - 1;
+    u32* base = sm + (long)warp * 2 * (n + 1) * Y;
+    auto val = [&](int poly, int m) -> u32* { return base + (long)(poly * (n + 1) + m) * Y; };
+    const u32* yk = a.y + k * npts * (long)g.ystride;
+    auto sgn = [&](int p) -> bool {
+        bool s = false;
+        if (a.su) s ^= a.su[k * npts + p] != 0;
+        if (a.sv) s ^= a.sv[k * npts + p] != 0;
+        return s;
+    };
+    chain_copy(yk, 2 * g.e, val(0, 0), Y);
+    chain_copy(nullptr, 0, val(1, 0), Y);
+    for (int m = 1; m <= n; ++m) {
+        const u32* Pp = yk + (2 * m - 1) * (long)g.ystride;
+        const u32* Mm = yk + (2 * m) * (long)g.ystride;
+        chain_even_odd(Pp, Mm, 2 * g.e, sgn(2 * m), m, val(0, m), val(1, m), Y);
+    }
+    __syncwarp();
+    for (int kk = 1; kk <= n; ++kk)
+        for (int m = n; m >= kk; --m)
+            for (int poly = 0; poly < 2; ++poly) {
+                const int R = m == kk ? 2 * (m - 1) : 2 * (m - kk - 1);
+                const bool div = m > kk;
+                chain_sub_shr_div(val(poly, m), val(poly, m - 1), val(poly, m), Y, R,
+                                  div ? dt.d[0][kk] : dt.d[0][0], div ? dt.d[1][kk] : dt.d[1][0]);
+                __syncwarp();
+            }
+    for (int m = n - 1; m >= 1; --m)
+        for (int kx = m; kx <= n - 1; ++kx)
+            for (int poly = 0; poly < 2; ++poly) {
+                chain_sub_shl(val(poly, kx), val(poly, kx + 1), val(poly, kx), Y, 2 * (m - 1));
+                __syncwarp();
+            }
+    // recompose: out[l] = sum_t w_t[l - t b], w_2i = ce_i, w_2i+1 = co_(i+1)
+    u32* out = a.out + k * a.out_stride;
+    const bool aligned = ((reinterpret_cast<uintptr_t>(out) & 15u) == 0);
+    SignedNorm st{0, 0};
+    const int nterms = 2 * n + 1;
+    for (int base_l = 0; base_l < a.out_len; base_l += CH) {
+        i64 cols[4];
+        const int l0 = base_l + 4 * lane;
+        int t0 = l0 / g.b;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int l = l0 + j;
+            u64 S = 0;
+            if (l < a.out_len) {
+                int t = t0;
+                while ((t + 1) * g.b <= l) ++t;  // t = floor(l / b)
+                if (t > nterms - 1) t = nterms - 1;
+                for (; t >= 0; --t) {
+                    const int x = l - t * g.b;
+                    if (x >= Y) break;
+                    S += val(t & 1, (t + 1) >> 1)[x];
+                }
+            }
+            cols[j] = (i64)S;
+        }
+        u32 d[4];
+        warp_norm_signed(cols, st, d);
+        if (aligned && l0 + 4 <= a.out_len) {
+            st4(out + l0, d);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (l0 + j < a.out_len) out[l0 + j] = d[j];
+        }
+    }
+}
+
 size_t interp_work_bytes(const LevelGeom& g) {
     const size_t bytes = (size_t)4 * (g.n + 1) * g.Y * 4;
     return bytes <= 160 * 1024 ? 0 : bytes;
@@ -557,6 +645,25 @@ cudaError_t launch_interp(const LevelGeom& g, const u32* y, const uint8_t* su, c
                           cudaStream_t st) {
     if (P <= 0) return cudaSuccess;
     static const DivTable dt = make_div_table();
+    // many small products: one warp per product
+    const size_t warp_smem = (size_t)2 * (g.n + 1) * g.Y * 4;
+    if (P >= 2048 && warp_smem <= 24 * 1024) {
+        InterpArgs a;
+        a.g = g; a.y = y; a.su = su; a.sv = sv; a.out = out; a.out_stride = out_stride;
+        a.out_len = out_len; a.work = nullptr; a.use_smem = 1;
+        int wpb = (int)((96 * 1024) / warp_smem);
+        if (wpb > 8) wpb = 8;
+        if (wpb < 1) wpb = 1;
+        static bool attr_w = false;
+        if (!attr_w) {
+            cudaFuncSetAttribute(interp_warp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 200 * 1024);
+            attr_w = true;
+        }
+        const long grid = (P + wpb - 1) / wpb;
+        interp_warp_kernel<<<(unsigned)grid, wpb * 32, wpb * warp_smem, st>>>(a, dt, P);
+        return cudaGetLastError();
+    }
     InterpArgs a;
     a.g = g;
     a.y = y;

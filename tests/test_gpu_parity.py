@@ -215,3 +215,80 @@ def test_batch_mixed_sizes(ctx, tc):
     tc.tc.tc_mul_batch(ctx, dev(A), a_off, la, dev(B), b_off, lb, OUT, o_off)
     want = native.schoolbook_batch(A, a_off, la, B, b_off, lb, o_off, int((la + lb).sum()))
     assert np.array_equal(host(OUT), want)
+
+
+# ---------------------------------------------------------------- base case, large batches
+# 4096 or more products select the lane-per-product kernel.
+
+@pytest.mark.parametrize("L", [1, 3, 7, 8, 9, 31, 63, 64, 65, 88, 100, 128, 137, 200])
+@pytest.mark.parametrize("layout", ["aligned", "strided"])
+def test_schoolbook_lane_kernel(tc, L, layout):
+    count = 4100
+    g = inputs.rng(L)
+    A = g.integers(0, 1 << 32, size=(count, L), dtype=np.uint64).astype(np.uint32)
+    B = g.integers(0, 1 << 32, size=(count, L), dtype=np.uint64).astype(np.uint32)
+    A[5] = 0xFFFFFFFF
+    B[5] = 0xFFFFFFFF
+    B[7] = 0
+    if layout == "strided":
+        dA = dev(np.pad(A, ((0, 0), (0, 3))))[:, :L]
+        dB = dev(np.pad(B, ((0, 0), (1, 0))))[:, 1:]
+    else:
+        dA, dB = dev(A), dev(B)
+    out = host(tc.tc.tc_schoolbook(dA, dB))
+    for k in list(range(0, count, 97)) + [5, 7, count - 1]:
+        assert np.array_equal(out[k], native.schoolbook(A[k], B[k])), (L, k)
+
+
+@pytest.mark.parametrize("L", [1, 2, 8, 9, 15, 16, 17, 64, 88, 130])
+def test_square_lane_kernel(tc, L):
+    count = 4200
+    g = inputs.rng(1000 + L)
+    A = g.integers(0, 1 << 32, size=(count, L), dtype=np.uint64).astype(np.uint32)
+    A[3] = 0xFFFFFFFF
+    dA = dev(A)
+    out = host(tc.tc.tc_schoolbook(dA, dA))
+    for k in list(range(0, count, 101)) + [3, count - 1]:
+        assert np.array_equal(out[k], native.schoolbook(A[k], A[k])), (L, k)
+
+
+# ---------------------------------------------------------------- many small interpolations
+# 2048 or more products with small values select the warp-per-product kernel.
+
+@pytest.mark.parametrize("B,L", [(2, 9), (3, 100), (4, 259), (8, 130), (3, 2)])
+def test_interpolate_many_products(tc, B, L):
+    import torch
+    count = 2100
+    _, e, _, ystride = tc.tc.level_sizes(L, B)
+    g = inputs.rng(7 * B + L)
+    A = g.integers(0, 1 << 32, size=(count, L), dtype=np.uint64).astype(np.uint32)
+    Bm = g.integers(0, 1 << 32, size=(count, L), dtype=np.uint64).astype(np.uint32)
+    A[1] = 0xFFFFFFFF
+    Bm[1] = 0xFFFFFFFF
+    Y = np.zeros((count, 2 * B - 1, ystride), dtype=np.uint32)
+    S = np.zeros((count, 2 * B - 1), dtype=np.uint8)
+    check = list(range(0, count, 53)) + [1, count - 1]
+    for k in range(count):
+        y = _oracle_level(to_int(A[k]), to_int(Bm[k]), L, B)
+        for p, val in enumerate(y):
+            Y[k, p, :2 * e] = from_int(abs(val), 2 * e)
+            S[k, p] = 1 if val < 0 else 0
+    out = host(tc.tc.tc_toom_interpolate(dev(Y), L, B, SGN_U=torch.from_numpy(S).cuda()))
+    for k in check:
+        assert same_limbs(out[k], to_int(A[k]) * to_int(Bm[k])), (B, L, k)
+
+
+@pytest.mark.parametrize("plan", [[16, 8, 3], [16, 4, 4], [8, 8, 4], [32, 8]])
+def test_uniform_batch_full_size_2e20(ctx, tc, plan):
+    """The benchmark's workload shape (2^20-bit operands) at a reduced batch,
+    with every level's kernels in their large-batch variants."""
+    L, count = 32768, 64
+    A = np.stack([inputs.uniform(L, 2 * k) for k in range(count)])
+    B = np.stack([inputs.uniform(L, 2 * k + 1) for k in range(count)])
+    A[3] = 0xFFFFFFFF
+    B[3] = 0xFFFFFFFF
+    OUT = host(tc.tc.tc_mul_uniform(ctx, dev(A), dev(B), plan=plan))
+    for k in (0, 3, 17, count - 1):
+        assert same_limbs(OUT[k], to_int(A[k]) * to_int(B[k])), (plan, k)
+    for k in range(count):
+        assert residues.product_residues_match(A[k], B[k], OUT[k]), (plan, k)
