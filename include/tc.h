@@ -168,16 +168,17 @@ tc_status tc_toom_evaluate(size_t count, size_t limbs, int B, const uint32_t *U,
  * magnitudes of 2e limbs at Y + (k*(2B-1) + p) * ystride with signs
  * SGN_U[k*(2B-1)+p] xor SGN_V[k*(2B-1)+p] (either may be NULL = all
  * positive); 2*limbs result limbs are written at OUT + k*ldo.  `work` is
- * device scratch of tc_toom_interpolate_work_bytes(...) * count bytes (may be
- * NULL when that is 0).  ystride >= 2e, multiple of 4.
+ * device scratch of tc_toom_interpolate_work_bytes(count, limbs, B) bytes (may
+ * be NULL when that is 0).  ystride >= 2e, multiple of 4.
  */
 tc_status tc_toom_interpolate(size_t count, size_t limbs, int B,
                               const uint32_t *Y, size_t ystride,
                               const uint8_t *SGN_U, const uint8_t *SGN_V,
                               uint32_t *OUT, size_t ldo, void *work, void *stream);
 
-/* Per-product scratch bytes of tc_toom_interpolate (0 when it runs in shared memory). */
-size_t tc_toom_interpolate_work_bytes(size_t limbs, int B);
+/* Scratch bytes tc_toom_interpolate needs for `count` products of `limbs`
+ * limbs split into B blocks (0 when it runs in shared memory). */
+size_t tc_toom_interpolate_work_bytes(size_t count, size_t limbs, int B);
 
 /* ---------------------------------------------------------------------
  * Serving: a request loop on a host thread that admits products while the

@@ -105,7 +105,7 @@ BatchLayout layout_for(size_t count, size_t s, const tc_opts& o, bool square) {
         L.sgnU.push_back(off); off = align256(off + (size_t)Pn);
         L.sgnV.push_back(off); if (!square) off = align256(off + (size_t)Pn);
         L.prod.push_back(off); off = align256(off + (size_t)Pn * g.ystride * 4);
-        L.work.push_back(off); off = align256(off + (size_t)P * interp_work_bytes(g));
+        L.work.push_back(off); off = align256(off + (size_t)P * interp_work_bytes(g, P));
         P = Pn;
         sl = g.e;
     }
@@ -223,7 +223,7 @@ tc_status run_uniform(const BatchLayout& L, char* base, size_t count, size_t s, 
         // squaring: every pointwise product U(x)^2 is non-negative, so no signs are passed
         const uint8_t* sU = square ? nullptr : reinterpret_cast<const uint8_t*>(base + L.sgnU[l]);
         const uint8_t* sV = square ? nullptr : reinterpret_cast<const uint8_t*>(base + L.sgnV[l]);
-        u32* work = interp_work_bytes(g) ? reinterpret_cast<u32*>(base + L.work[l]) : nullptr;
+        u32* work = interp_work_bytes(g, L.P[l]) ? reinterpret_cast<u32*>(base + L.work[l]) : nullptr;
         pt.begin(2, l, 4.0 * L.P[l] * ((2.0 * g.B - 1) * 2 * g.e + 2.0 * g.s) +
                            (square ? 0.0 : 2.0 * (2 * g.B - 1) * L.P[l]), 0);
         CK(launch_interp(g, reinterpret_cast<const u32*>(base + L.prod[l]), sU, sV, out, ostr,
@@ -591,9 +591,9 @@ extern "C" tc_status tc_toom_evaluate(size_t count, size_t limbs, int B, const u
     return TC_OK;
 }
 
-extern "C" size_t tc_toom_interpolate_work_bytes(size_t limbs, int B) {
-    if (B < 2 || B > 32 || limbs == 0) return 0;
-    return interp_work_bytes(make_level((int)limbs, B));
+extern "C" size_t tc_toom_interpolate_work_bytes(size_t count, size_t limbs, int B) {
+    if (B < 2 || B > 32 || limbs == 0 || limbs > (1u << 30)) return 0;
+    return count * interp_work_bytes(make_level((int)limbs, B), (long)count);
 }
 
 extern "C" tc_status tc_toom_interpolate(size_t count, size_t limbs, int B, const uint32_t* Y,
@@ -605,7 +605,7 @@ extern "C" tc_status tc_toom_interpolate(size_t count, size_t limbs, int B, cons
     LevelGeom g = make_level((int)limbs, B);
     if (ystride < (size_t)(2 * g.e) || ystride % 4) return TC_EINVAL;
     if (count > 1 && ldo < 2 * limbs) return TC_EINVAL;
-    if (interp_work_bytes(g) && !work) return TC_EINVAL;
+    if (interp_work_bytes(g, (long)count) && !work) return TC_EINVAL;
     g.ystride = (int)ystride;
     CK(launch_interp(g, Y, SGN_U, SGN_V, OUT, (long)ldo, 2 * g.s, (u32*)work, (long)count,
                      (cudaStream_t)stream));

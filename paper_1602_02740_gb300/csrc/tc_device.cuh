@@ -61,54 +61,6 @@ __device__ __forceinline__ u32 warp_carry_scan(bool g, bool p, u32 cin, u32* cou
 }
 
 // ---------------------------------------------------------------------------
-// 4-limb add/sub with carry, as plain 64-bit arithmetic.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ u32 add4(const u32 a[4], const u32 b[4], u32 cin, u32 r[4]) {
-    u64 c = cin;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        u64 t = (u64)a[j] + b[j] + c;
-        r[j] = (u32)t;
-        c = t >> 32;
-    }
-    return (u32)c;
-}
-
-__device__ __forceinline__ u32 sub4(const u32 a[4], const u32 b[4], u32 bin, u32 r[4]) {
-    u64 bw = bin;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        u64 t = (u64)a[j] - b[j] - bw;
-        r[j] = (u32)t;
-        bw = (t >> 32) & 1u;
-    }
-    return (u32)bw;
-}
-
-__device__ __forceinline__ bool all_zero4(const u32 r[4]) { return (r[0] | r[1] | r[2] | r[3]) == 0u; }
-__device__ __forceinline__ bool all_ones4(const u32 r[4]) { return (r[0] & r[1] & r[2] & r[3]) == FULL; }
-
-// Warp-wide a + b + cin over one chunk; cin/cout are warp-uniform carries.
-__device__ __forceinline__ void warp_add_chunk(const u32 a[4], const u32 b[4], u32& carry, u32 r[4]) {
-    u32 g = add4(a, b, 0u, r);
-    bool p = !g && all_ones4(r);
-    u32 cout;
-    u32 cin = warp_carry_scan(g != 0u, p, carry, &cout);
-    add4(a, b, cin, r);
-    carry = cout;
-}
-
-// Warp-wide a - b - bin over one chunk.
-__device__ __forceinline__ void warp_sub_chunk(const u32 a[4], const u32 b[4], u32& borrow, u32 r[4]) {
-    u32 g = sub4(a, b, 0u, r);
-    bool p = !g && all_zero4(r);
-    u32 bout;
-    u32 bin = warp_carry_scan(g != 0u, p, borrow, &bout);
-    sub4(a, b, bin, r);
-    borrow = bout;
-}
-
-// ---------------------------------------------------------------------------
 // Normalisation of signed column sums.
 //
 // A value given as sum_l col[l] 2^(32 l) with |col| < 2^62 is turned into
@@ -182,58 +134,144 @@ __device__ __forceinline__ void warp_norm_signed(const i64 cols[4], SignedNorm& 
 }
 
 // ---------------------------------------------------------------------------
-// Exact division by an odd constant d < 2^32 (multiply by d^-1 mod 2^32,
-// Jebelean / Granlund-Montgomery style), chunk-parallel.
+// Exact division by an odd constant d < 2^31 (multiply by d^-1 mod 2^32, the
+// Jebelean / Granlund-Montgomery exact division), chunk-parallel.
 //
 // Serial step on limb a with borrow B: x = a - B (mod 2^32), q = x d^-1,
 // B' = hi32(q d) + [a < B].  For an exact quotient the borrow entering limb
 // position p is B_p = (-(a mod 2^(32p)) 2^(-32p)) mod d, so across a lane of
-// four limbs B_out = (B_out(0) + B_in rho^4) mod d with rho = 2^-32 mod d.
-// That affine recurrence is scanned across the warp; then each lane reruns
-// its four serial steps from its true borrow.
+// KL limbs B_out = (B_out(0) + B_in rho^KL) mod d with rho = 2^-32 mod d.
+// That affine recurrence, with the same multiplier in every lane, is scanned
+// across the warp (Kogge-Stone, multiplier rho^(KL 2^i) at step i); then each
+// lane reruns its serial steps from its true borrow.  The modular products
+// of the scan use Montgomery reduction with R = 2^32.
 // ---------------------------------------------------------------------------
 struct DivConst {
-    u32 d;       // odd divisor (1 = no division)
+    u32 d;       // odd divisor (1 = no division), d < 2^31
     u32 inv;     // d^-1 mod 2^32
-    u64 magic;   // floor(2^64 / d) for Barrett reduction
-    u32 rk[5];   // (rho^4)^(2^i) mod d, i = 0..4
+    u32 ninv;    // -d^-1 mod 2^32
+    u32 rkm[5];  // (rho^KL)^(2^i) 2^32 mod d: Montgomery form of the scan multipliers
 };
 
-__device__ __forceinline__ u32 mod_reduce(u64 x, u32 d, u64 magic) {
-    u64 q = __umul64hi(x, magic);
-    u64 r = x - q * (u64)d;
-    return (u32)(r >= d ? r - d : r);
-}
-
-__device__ __forceinline__ u32 mod_mul(u32 a, u32 b, u32 d, u64 magic) {
-    return mod_reduce((u64)a * b, d, magic);
+// Montgomery product a b 2^-32 mod d for a, b < d < 2^31.
+__device__ __forceinline__ u32 mont_mul(u32 a, u32 b, u32 d, u32 ninv) {
+    const u64 t = (u64)a * b;
+    const u32 m = (u32)t * ninv;
+    const u64 u = ((u64)m * d + t) >> 32;  // t + m d < 2^64 since d < 2^31
+    const u32 r = (u32)u;
+    return r >= d ? r - d : r;
 }
 
 __device__ __forceinline__ u32 div_step(u32 a, u32 B, u32 d, u32 inv, u32& q) {
-    u32 x = a - B;
+    const u32 x = a - B;
     q = x * inv;
     return __umulhi(q, d) + (a < B ? 1u : 0u);
 }
 
-// In-place exact division of this warp's chunk v (4 limbs per lane).
-// `borrow` is the warp-uniform borrow entering the chunk; updated on return.
-__device__ __forceinline__ void warp_exact_div_chunk(u32 v[4], const DivConst& dc, u32& borrow) {
+// ---------------------------------------------------------------------------
+// The same primitives for KL limbs per lane (chunks of 32 KL limbs).
+// ---------------------------------------------------------------------------
+template <int KL>
+__device__ __forceinline__ void ld_seg(const u32* p, u32 v[KL]) {
+#pragma unroll
+    for (int j = 0; j < KL; j += 4) {
+        const uint4 q = ld4(p + j);
+        v[j] = q.x; v[j + 1] = q.y; v[j + 2] = q.z; v[j + 3] = q.w;
+    }
+}
+
+template <int KL>
+__device__ __forceinline__ void st_seg(u32* p, const u32 v[KL]) {
+#pragma unroll
+    for (int j = 0; j < KL; j += 4) st4(p + j, v + j);
+}
+
+// KL limbs at `pos` of a row with `len` valid limbs (zeros beyond); row 16-byte aligned.
+template <int KL>
+__device__ __forceinline__ void ld_seg_masked(const u32* row, int pos, int len, u32 v[KL]) {
+#pragma unroll
+    for (int j = 0; j < KL; j += 4) ld4_masked(row, pos + j, len, v + j);
+}
+
+template <int KL>
+__device__ __forceinline__ u32 add_seg(const u32 a[KL], const u32 b[KL], u32 cin, u32 r[KL]) {
+    u64 c = cin;
+#pragma unroll
+    for (int j = 0; j < KL; ++j) {
+        const u64 t = (u64)a[j] + b[j] + c;
+        r[j] = (u32)t;
+        c = t >> 32;
+    }
+    return (u32)c;
+}
+
+template <int KL>
+__device__ __forceinline__ u32 sub_seg(const u32 a[KL], const u32 b[KL], u32 bin, u32 r[KL]) {
+    u64 bw = bin;
+#pragma unroll
+    for (int j = 0; j < KL; ++j) {
+        const u64 t = (u64)a[j] - b[j] - bw;
+        r[j] = (u32)t;
+        bw = (t >> 32) & 1u;
+    }
+    return (u32)bw;
+}
+
+template <int KL>
+__device__ __forceinline__ bool zero_seg(const u32 r[KL]) {
+    u32 x = 0;
+#pragma unroll
+    for (int j = 0; j < KL; ++j) x |= r[j];
+    return x == 0u;
+}
+
+template <int KL>
+__device__ __forceinline__ bool ones_seg(const u32 r[KL]) {
+    u32 x = FULL;
+#pragma unroll
+    for (int j = 0; j < KL; ++j) x &= r[j];
+    return x == FULL;
+}
+
+template <int KL>
+__device__ __forceinline__ void warp_add_seg(const u32 a[KL], const u32 b[KL], u32& carry, u32 r[KL]) {
+    const u32 g = add_seg<KL>(a, b, 0u, r);
+    const bool p = !g && ones_seg<KL>(r);
+    u32 cout;
+    const u32 cin = warp_carry_scan(g != 0u, p, carry, &cout);
+    if (cin) add_seg<KL>(a, b, 1u, r);
+    carry = cout;
+}
+
+template <int KL>
+__device__ __forceinline__ void warp_sub_seg(const u32 a[KL], const u32 b[KL], u32& borrow, u32 r[KL]) {
+    const u32 g = sub_seg<KL>(a, b, 0u, r);
+    const bool p = !g && zero_seg<KL>(r);
+    u32 bout;
+    const u32 bin = warp_carry_scan(g != 0u, p, borrow, &bout);
+    if (bin) sub_seg<KL>(a, b, 1u, r);
+    borrow = bout;
+}
+
+// Exact division of a warp chunk of 32 KL limbs by dc.d (constants built for this KL).
+template <int KL>
+__device__ __forceinline__ void warp_exact_div_seg(u32 v[KL], const DivConst& dc, u32& borrow) {
     const int lane = lane_id();
     u32 q;
     u32 b0 = 0;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) b0 = div_step(v[j], b0, dc.d, dc.inv, q);
+    for (int j = 0; j < KL; ++j) b0 = div_step(v[j], b0, dc.d, dc.inv, q);
     u32 t = b0;
     if (lane == 0) {
-        u32 x = mod_mul(borrow, dc.rk[0], dc.d, dc.magic) + t;
+        const u32 x = mont_mul(borrow, dc.rkm[0], dc.d, dc.ninv) + t;
         t = x >= dc.d ? x - dc.d : x;
     }
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
-        int s = 1 << i;
-        u32 o = __shfl_up_sync(FULL, t, s);
+        const int s = 1 << i;
+        const u32 o = __shfl_up_sync(FULL, t, s);
         if (lane >= s) {
-            u32 x = mod_mul(o, dc.rk[i], dc.d, dc.magic) + t;
+            const u32 x = mont_mul(o, dc.rkm[i], dc.d, dc.ninv) + t;
             t = x >= dc.d ? x - dc.d : x;
         }
     }
@@ -241,7 +279,7 @@ __device__ __forceinline__ void warp_exact_div_chunk(u32 v[4], const DivConst& d
     if (lane == 0) bin = borrow;
     u32 B = bin;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < KL; ++j) {
         B = div_step(v[j], B, dc.d, dc.inv, q);
         v[j] = q;
     }

@@ -14,7 +14,8 @@ struct LevelGeom {
     int e;         // evaluation length = b + ceil((n(n-1)+1)/32)
     int estride;   // evaluation row stride: roundup(e, 4)
     int ystride;   // pointwise-product row stride: roundup(2e, 4)
-    int Y;         // interpolation value length: roundup(2e + 2, 128)
+    int K;         // limbs per lane in interpolation passes (4 or 8)
+    int Y;         // interpolation value length: roundup(2e + 2, 32 K)
 };
 
 LevelGeom make_level(int s, int B);
@@ -31,8 +32,8 @@ cudaError_t launch_leaf(const uint32_t* A, long lda, const uint32_t* Bm, long ld
 cudaError_t launch_eval(const uint32_t* in, long in_stride, const LevelGeom& g,
                         uint32_t* out, uint8_t* sgn, long P, cudaStream_t st);
 
-// Per-product bytes of global work the interpolation needs (0 = shared memory).
-size_t interp_work_bytes(const LevelGeom& g);
+// Per-product bytes of global work the interpolation of P products needs (0 = shared memory).
+size_t interp_work_bytes(const LevelGeom& g, long P);
 
 cudaError_t launch_interp(const LevelGeom& g, const uint32_t* y, const uint8_t* su,
                           const uint8_t* sv, uint32_t* out, long out_stride, int out_len,

@@ -21,7 +21,9 @@ LevelGeom make_level(int s, int B) {
     g.e = g.b + (g.n * (g.n - 1) + 1 + 31) / 32;
     g.estride = (g.e + 3) / 4 * 4;
     g.ystride = (2 * g.e + 3) / 4 * 4;
-    g.Y = (2 * g.e + 2 + CH - 1) / CH * CH;
+    const int need = 2 * g.e + 2;
+    g.K = need > 1536 ? 8 : 4;  // limbs per lane in interpolation passes
+    g.Y = (need + 32 * g.K - 1) / (32 * g.K) * (32 * g.K);
     return g;
 }
 
@@ -178,30 +180,32 @@ static u32 powmod_host(u64 base, u64 e, u32 m) {
     return (u32)r;
 }
 
-static DivConst make_div(u32 d) {
+// Constants for exact division by odd d with KL limbs per lane.
+static DivConst make_div(u32 d, int KL) {
     DivConst c;
     c.d = d;
     c.inv = inv32(d);
-    c.magic = d > 1 ? ~0ull / d : 0ull;
+    c.ninv = 0u - c.inv;
+    for (int i = 0; i < 5; ++i) c.rkm[i] = 0;
     if (d > 1) {
-        // rk[0] = rho^4 = 2^-128 mod d: the inverse of 2^128 mod d by extended Euclid.
-        u32 two128 = powmod_host(2, 128, d);
-        i64 a = two128, m = d, x0 = 1, x1 = 0;
+        // rk = rho^KL = 2^(-32 KL) mod d: the inverse of 2^(32 KL) mod d by extended Euclid.
+        const u32 t = powmod_host(2, 32ull * KL, d);
+        i64 a = t, m = d, x0 = 1, x1 = 0;
         while (m) {
-            i64 q = a / m, t = a - q * m;
-            a = m; m = t;
-            t = x0 - q * x1; x0 = x1; x1 = t;
+            i64 q = a / m, r = a - q * m;
+            a = m; m = r;
+            r = x0 - q * x1; x0 = x1; x1 = r;
         }
-        u32 rk = (u32)((x0 % (i64)d + d) % d);
-        c.rk[0] = rk;
-        for (int i = 1; i < 5; ++i) c.rk[i] = (u32)((u64)c.rk[i - 1] * c.rk[i - 1] % d);
-    } else {
-        for (int i = 0; i < 5; ++i) c.rk[i] = 0;
+        u64 rk = (u64)((x0 % (i64)d + d) % d);
+        for (int i = 0; i < 5; ++i) {
+            c.rkm[i] = (u32)((rk << 32) % d);
+            rk = rk * rk % d;
+        }
     }
     return c;
 }
 
-static DivTable make_div_table() {
+static DivTable make_div_table(int KL) {
     DivTable t;
     for (int k = 0; k < 32; ++k) {
         u32 d1 = 1, d2 = 1;
@@ -210,142 +214,213 @@ static DivTable make_div_table() {
             d1 = (u32)((1ull << k) - 1);
             d2 = (u32)((1ull << k) + 1);
         }
-        t.d[0][k] = make_div(d1);
-        t.d[1][k] = make_div(d2);
+        t.d[0][k] = make_div(d1, KL);
+        t.d[1][k] = make_div(d2, KL);
     }
     return t;
 }
 
-// Shifted emission of chunk c-1.  w0..w3: this lane's limbs of the chunk;
-// below: the limb under w0; a0, a1: the two limbs above w3.  sh < 0 shifts
-// right by -sh (< 64), sh >= 0 shifts left by sh (< 32).
-__device__ __forceinline__ void shift_window(const u32 w[4], u32 below, u32 a0, u32 a1, int sh,
-                                             u32 out[4]) {
-    const u32 x[7] = {below, w[0], w[1], w[2], w[3], a0, a1};  // x[i + 1] = limb i
+// Shifted emission: w = this lane's KL limbs; below = the limb under w[0];
+// a0, a1 = the two limbs above w[KL-1].  sh < 0 shifts right by -sh (< 64),
+// sh >= 0 shifts left by sh (< 32).
+template <int KL>
+__device__ __forceinline__ void shift_window(const u32 w[KL], u32 below, u32 a0, u32 a1, int sh,
+                                             u32 out[KL]) {
+    u32 x[KL + 3];  // x[i + 1] = limb i
+    x[0] = below;
+#pragma unroll
+    for (int j = 0; j < KL; ++j) x[j + 1] = w[j];
+    x[KL + 1] = a0;
+    x[KL + 2] = a1;
     if (sh < 0) {
         const int R = -sh, qa = R >> 5, r = R & 31;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < KL; ++j) {
             const u32 lo = qa ? x[j + 2] : x[j + 1];
             const u32 hi = qa ? x[j + 3] : x[j + 2];
             out[j] = fshr(lo, hi, (u32)r);
         }
     } else {
 #pragma unroll
-        for (int j = 0; j < 4; ++j) out[j] = fshl(x[j], x[j + 1], (u32)sh);
+        for (int j = 0; j < KL; ++j) out[j] = fshl(x[j], x[j + 1], (u32)sh);
     }
 }
 
-// c_out = ((X - Z) >> R) / d1 / d2   (R < 64; d == 1 means no division)
-__device__ void chain_sub_shr_div(const u32* X, const u32* Z, u32* O, int Y, int R,
-                                  const DivConst& d1, const DivConst& d2) {
+// Two chains at once (the even and the odd polynomial share every shift and
+// divisor): O_p = ((X_p - Z_p) >> R) / d1 / d2 for p = 0, 1.  R < 64; a
+// divisor of 1 means no division.  The two chains are independent, so their
+// scans and multiply chains interleave.
+template <int KL>
+__device__ void chain2_sub_shr_div(const u32* X0, const u32* Z0, u32* O0, const u32* X1,
+                                   const u32* Z1, u32* O1, int Y, int R, const DivConst& d1,
+                                   const DivConst& d2) {
+    constexpr int C = 32 * KL;
     const int lane = lane_id();
-    const int nch = Y / CH;
-    u32 bw = 0, B1 = 0, B2 = 0;
-    u32 prev[4] = {0, 0, 0, 0};
+    const int nch = Y / C;
+    const u32* X[2] = {X0, X1};
+    const u32* Z[2] = {Z0, Z1};
+    u32* O[2] = {O0, O1};
+    u32 bw[2] = {0, 0}, B1[2] = {0, 0}, B2[2] = {0, 0};
+    u32 prev[2][KL];
+#pragma unroll
+    for (int p = 0; p < 2; ++p)
+#pragma unroll
+        for (int j = 0; j < KL; ++j) prev[p][j] = 0;
     for (int c = 0; c <= nch; ++c) {
-        u32 cur[4] = {0, 0, 0, 0};
+        u32 cur[2][KL];
         if (c < nch) {
-            uint4 xv = ld4(X + c * CH + 4 * lane), zv = ld4(Z + c * CH + 4 * lane);
-            const u32 x[4] = {xv.x, xv.y, xv.z, xv.w}, z[4] = {zv.x, zv.y, zv.z, zv.w};
-            warp_sub_chunk(x, z, bw, cur);
+            u32 x[2][KL], z[2][KL];
+#pragma unroll
+            for (int p = 0; p < 2; ++p) {
+                ld_seg<KL>(X[p] + c * C + KL * lane, x[p]);
+                ld_seg<KL>(Z[p] + c * C + KL * lane, z[p]);
+            }
+#pragma unroll
+            for (int p = 0; p < 2; ++p) warp_sub_seg<KL>(x[p], z[p], bw[p], cur[p]);
+        } else {
+#pragma unroll
+            for (int p = 0; p < 2; ++p)
+#pragma unroll
+                for (int j = 0; j < KL; ++j) cur[p][j] = 0;
         }
         if (c > 0) {
-            u32 a0 = __shfl_down_sync(FULL, prev[0], 1), a1 = __shfl_down_sync(FULL, prev[1], 1);
-            const u32 c0 = __shfl_sync(FULL, cur[0], 0), c1 = __shfl_sync(FULL, cur[1], 0);
-            if (lane == 31) { a0 = c0; a1 = c1; }
-            u32 v[4];
-            shift_window(prev, 0u, a0, a1, -R, v);
-            if (d1.d > 1) warp_exact_div_chunk(v, d1, B1);
-            if (d2.d > 1) warp_exact_div_chunk(v, d2, B2);
-            st4(O + (c - 1) * CH + 4 * lane, v);
+            u32 v[2][KL];
+#pragma unroll
+            for (int p = 0; p < 2; ++p) {
+                u32 a0 = __shfl_down_sync(FULL, prev[p][0], 1), a1 = __shfl_down_sync(FULL, prev[p][1], 1);
+                const u32 c0 = __shfl_sync(FULL, cur[p][0], 0), c1 = __shfl_sync(FULL, cur[p][1], 0);
+                if (lane == 31) { a0 = c0; a1 = c1; }
+                shift_window<KL>(prev[p], 0u, a0, a1, -R, v[p]);
+            }
+            if (d1.d > 1) {
+#pragma unroll
+                for (int p = 0; p < 2; ++p) warp_exact_div_seg<KL>(v[p], d1, B1[p]);
+            }
+            if (d2.d > 1) {
+#pragma unroll
+                for (int p = 0; p < 2; ++p) warp_exact_div_seg<KL>(v[p], d2, B2[p]);
+            }
+#pragma unroll
+            for (int p = 0; p < 2; ++p) st_seg<KL>(O[p] + (c - 1) * C + KL * lane, v[p]);
         }
 #pragma unroll
-        for (int j = 0; j < 4; ++j) prev[j] = cur[j];
+        for (int p = 0; p < 2; ++p)
+#pragma unroll
+            for (int j = 0; j < KL; ++j) prev[p][j] = cur[p][j];
     }
 }
 
-// c_out = X - (Z << S)   (S < 64)
-__device__ void chain_sub_shl(const u32* X, const u32* Z, u32* O, int Y, int S) {
+// Two chains at once: O_p = X_p - (Z_p << S), p = 0, 1 (S < 64).
+template <int KL>
+__device__ void chain2_sub_shl(const u32* X0, const u32* Z0, u32* O0, const u32* X1,
+                               const u32* Z1, u32* O1, int Y, int S) {
+    constexpr int C = 32 * KL;
     const int lane = lane_id();
-    const int nch = Y / CH;
+    const int nch = Y / C;
     const int qa = S >> 5, s = S & 31;
-    u32 bw = 0, t2 = 0, t3 = 0;
+    const u32* X[2] = {X0, X1};
+    const u32* Z[2] = {Z0, Z1};
+    u32* O[2] = {O0, O1};
+    u32 bw[2] = {0, 0}, t2[2] = {0, 0}, t3[2] = {0, 0};
     for (int c = 0; c < nch; ++c) {
-        uint4 xv = ld4(X + c * CH + 4 * lane), zv = ld4(Z + c * CH + 4 * lane);
-        const u32 x[4] = {xv.x, xv.y, xv.z, xv.w};
-        u32 m1 = __shfl_up_sync(FULL, zv.w, 1), m2 = __shfl_up_sync(FULL, zv.z, 1);
-        if (lane == 0) { m1 = t3; m2 = t2; }
-        const u32 zw[6] = {m2, m1, zv.x, zv.y, zv.z, zv.w};  // zw[i + 2] = limb i
-        u32 sz[4];
+        u32 x[2][KL], z[2][KL];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const u32 hi = qa ? zw[j + 1] : zw[j + 2];
-            const u32 lo = qa ? zw[j] : zw[j + 1];
-            sz[j] = fshl(lo, hi, (u32)s);
+        for (int p = 0; p < 2; ++p) {
+            ld_seg<KL>(X[p] + c * C + KL * lane, x[p]);
+            ld_seg<KL>(Z[p] + c * C + KL * lane, z[p]);
         }
-        u32 r[4];
-        warp_sub_chunk(x, sz, bw, r);
-        st4(O + c * CH + 4 * lane, r);
-        t3 = __shfl_sync(FULL, zv.w, 31);
-        t2 = __shfl_sync(FULL, zv.z, 31);
+        u32 r[2][KL];
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+            u32 m1 = __shfl_up_sync(FULL, z[p][KL - 1], 1), m2 = __shfl_up_sync(FULL, z[p][KL - 2], 1);
+            if (lane == 0) { m1 = t3[p]; m2 = t2[p]; }
+            u32 zw[KL + 2];  // zw[i + 2] = limb i
+            zw[0] = m2;
+            zw[1] = m1;
+#pragma unroll
+            for (int j = 0; j < KL; ++j) zw[j + 2] = z[p][j];
+            u32 sz[KL];
+#pragma unroll
+            for (int j = 0; j < KL; ++j) {
+                const u32 hi = qa ? zw[j + 1] : zw[j + 2];
+                const u32 lo = qa ? zw[j] : zw[j + 1];
+                sz[j] = fshl(lo, hi, (u32)s);
+            }
+            warp_sub_seg<KL>(x[p], sz, bw[p], r[p]);
+        }
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+            st_seg<KL>(O[p] + c * C + KL * lane, r[p]);
+            t3[p] = __shfl_sync(FULL, z[p][KL - 1], 31);
+            t2[p] = __shfl_sync(FULL, z[p][KL - 2], 31);
+        }
     }
 }
 
 // Even-odd combine for node m >= 1 (eq. 4.5-4.6):
 //   A = W(x) + |W(-x)|, D = W(x) - |W(-x)|  (W(x) >= |W(-x)|)
 //   ye_m = (neg ? D : A) / 2,   yo_m = x (neg ? A : D) / 2,  x = 2^(m-1)
+template <int KL>
 __device__ void chain_even_odd(const u32* Pp, const u32* Mm, int len, bool neg, int m,
                                u32* CE, u32* CO, int Y) {
+    constexpr int C = 32 * KL;
     const int lane = lane_id();
-    const int nch = Y / CH;
+    const int nch = Y / C;
     u32 cA = 0, bD = 0;
-    u32 pA[4] = {0, 0, 0, 0}, pD[4] = {0, 0, 0, 0};
+    u32 pA[KL], pD[KL];
+#pragma unroll
+    for (int j = 0; j < KL; ++j) { pA[j] = 0; pD[j] = 0; }
     u32 tA = 0, tD = 0;  // last limb of chunk c-2
     const int sh_o = m == 1 ? -1 : m - 2;
     for (int c = 0; c <= nch; ++c) {
-        u32 A[4] = {0, 0, 0, 0}, D[4] = {0, 0, 0, 0};
+        u32 A[KL], D[KL];
         if (c < nch) {
-            u32 p[4], q[4];
-            ld4_masked(Pp, c * CH + 4 * lane, len, p);
-            ld4_masked(Mm, c * CH + 4 * lane, len, q);
-            warp_add_chunk(p, q, cA, A);
-            warp_sub_chunk(p, q, bD, D);
+            u32 p[KL], q[KL];
+            ld_seg_masked<KL>(Pp, c * C + KL * lane, len, p);
+            ld_seg_masked<KL>(Mm, c * C + KL * lane, len, q);
+            warp_add_seg<KL>(p, q, cA, A);
+            warp_sub_seg<KL>(p, q, bD, D);
+        } else {
+#pragma unroll
+            for (int j = 0; j < KL; ++j) { A[j] = 0; D[j] = 0; }
         }
         if (c > 0) {
-            // neighbours for both candidate values
-            u32 bA = __shfl_up_sync(FULL, pA[3], 1), bDv = __shfl_up_sync(FULL, pD[3], 1);
+            u32 bA = __shfl_up_sync(FULL, pA[KL - 1], 1), bDv = __shfl_up_sync(FULL, pD[KL - 1], 1);
             if (lane == 0) { bA = tA; bDv = tD; }
             u32 aA0 = __shfl_down_sync(FULL, pA[0], 1), aA1 = __shfl_down_sync(FULL, pA[1], 1);
             u32 aD0 = __shfl_down_sync(FULL, pD[0], 1), aD1 = __shfl_down_sync(FULL, pD[1], 1);
             const u32 nA0 = __shfl_sync(FULL, A[0], 0), nA1 = __shfl_sync(FULL, A[1], 0);
             const u32 nD0 = __shfl_sync(FULL, D[0], 0), nD1 = __shfl_sync(FULL, D[1], 0);
             if (lane == 31) { aA0 = nA0; aA1 = nA1; aD0 = nD0; aD1 = nD1; }
-            u32 e_out[4], o_out[4];
+            u32 e_out[KL], o_out[KL];
             if (neg) {
-                shift_window(pD, bDv, aD0, aD1, -1, e_out);
-                shift_window(pA, bA, aA0, aA1, sh_o, o_out);
+                shift_window<KL>(pD, bDv, aD0, aD1, -1, e_out);
+                shift_window<KL>(pA, bA, aA0, aA1, sh_o, o_out);
             } else {
-                shift_window(pA, bA, aA0, aA1, -1, e_out);
-                shift_window(pD, bDv, aD0, aD1, sh_o, o_out);
+                shift_window<KL>(pA, bA, aA0, aA1, -1, e_out);
+                shift_window<KL>(pD, bDv, aD0, aD1, sh_o, o_out);
             }
-            st4(CE + (c - 1) * CH + 4 * lane, e_out);
-            st4(CO + (c - 1) * CH + 4 * lane, o_out);
+            st_seg<KL>(CE + (c - 1) * C + KL * lane, e_out);
+            st_seg<KL>(CO + (c - 1) * C + KL * lane, o_out);
         }
-        tA = __shfl_sync(FULL, pA[3], 31);
-        tD = __shfl_sync(FULL, pD[3], 31);
+        tA = __shfl_sync(FULL, pA[KL - 1], 31);
+        tD = __shfl_sync(FULL, pD[KL - 1], 31);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) { pA[j] = A[j]; pD[j] = D[j]; }
+        for (int j = 0; j < KL; ++j) { pA[j] = A[j]; pD[j] = D[j]; }
     }
 }
 
 // Copy a row of `len` limbs into a value of Y limbs (zero-extended); zero if src == null.
+template <int KL>
 __device__ void chain_copy(const u32* src, int len, u32* dst, int Y) {
+    constexpr int C = 32 * KL;
     const int lane = lane_id();
-    for (int c = 0; c < Y; c += CH) {
-        u32 v[4] = {0, 0, 0, 0};
-        if (src) ld4_masked(src, c + 4 * lane, len, v);
-        st4(dst + c + 4 * lane, v);
+    for (int c = 0; c < Y; c += C) {
+        u32 v[KL];
+#pragma unroll
+        for (int j = 0; j < KL; ++j) v[j] = 0;
+        if (src) ld_seg_masked<KL>(src, c + KL * lane, len, v);
+        st_seg<KL>(dst + c + KL * lane, v);
     }
 }
 
@@ -463,7 +538,8 @@ struct InterpArgs {
     int use_smem;
 };
 
-__global__ void __launch_bounds__(1024)
+template <int KL>
+__global__ void __launch_bounds__(512)
 interp_kernel(InterpArgs a, DivTable dt, long P) {
     extern __shared__ __align__(16) u32 sm[];
     const long k = blockIdx.x;
@@ -493,56 +569,53 @@ interp_kernel(InterpArgs a, DivTable dt, long P) {
     // ---- even-odd combine (chain 0: node 0) ----
     for (int c = warp; c <= n; c += nw) {
         if (c == 0) {
-            chain_copy(yk, 2 * g.e, val(0, 0, 0), Y);
-            chain_copy(nullptr, 0, val(0, 1, 0), Y);
+            chain_copy<KL>(yk, 2 * g.e, val(0, 0, 0), Y);
+            chain_copy<KL>(nullptr, 0, val(0, 1, 0), Y);
         } else {
             const u32* Pp = yk + (2 * c - 1) * (long)g.ystride;
             const u32* Mm = yk + (2 * c) * (long)g.ystride;
-            chain_even_odd(Pp, Mm, 2 * g.e, sgn(2 * c), c, val(0, 0, c), val(0, 1, c), Y);
+            chain_even_odd<KL>(Pp, Mm, 2 * g.e, sgn(2 * c), c, val(0, 0, c), val(0, 1, c), Y);
         }
     }
     __syncthreads();
 
-    // ---- Newton loop 1 (Theorem 3.2) ----
+    // ---- Newton loop 1 (Theorem 3.2); both polynomials in one warp ----
+    // (the two polynomials' slots move together, so slot[0][.] serves both)
     for (int kk = 1; kk <= n; ++kk) {
         const int cnt = n - kk + 1;
-        for (int c = warp; c < 2 * cnt; c += nw) {
-            const int poly = c / cnt, m = kk + c % cnt;
-            const int sx = slot[poly][m], sz = slot[poly][m - 1];
+        for (int c = warp; c < cnt; c += nw) {
+            const int m = kk + c;
+            const int sx = slot[0][m], sz = slot[0][m - 1];
             const int R = m == kk ? 2 * (m - 1) : 2 * (m - kk - 1);
             const bool div = m > kk;
-            chain_sub_shr_div(val(sx, poly, m), val(sz, poly, m - 1), val(1 - sx, poly, m), Y, R,
-                              div ? dt.d[0][kk] : dt.d[0][0], div ? dt.d[1][kk] : dt.d[1][0]);
+            chain2_sub_shr_div<KL>(val(sx, 0, m), val(sz, 0, m - 1), val(1 - sx, 0, m),
+                                   val(sx, 1, m), val(sz, 1, m - 1), val(1 - sx, 1, m), Y, R,
+                                   div ? dt.d[0][kk] : dt.d[0][0], div ? dt.d[1][kk] : dt.d[1][0]);
         }
         __syncthreads();
-        if (tid < 2 * cnt) {
-            const int poly = tid / cnt, m = kk + tid % cnt;
-            slot[poly][m] ^= 1;
-        }
+        if (tid < cnt) slot[0][kk + tid] ^= 1;
         __syncthreads();
     }
 
     // ---- Newton loop 2 (Theorem 3.3) ----
     for (int m = n - 1; m >= 1; --m) {
         const int cnt = n - m;
-        for (int c = warp; c < 2 * cnt; c += nw) {
-            const int poly = c / cnt, kx = m + c % cnt;
-            const int sx = slot[poly][kx], sz = slot[poly][kx + 1];
-            chain_sub_shl(val(sx, poly, kx), val(sz, poly, kx + 1), val(1 - sx, poly, kx), Y,
-                          2 * (m - 1));
+        for (int c = warp; c < cnt; c += nw) {
+            const int kx = m + c;
+            const int sx = slot[0][kx], sz = slot[0][kx + 1];
+            chain2_sub_shl<KL>(val(sx, 0, kx), val(sz, 0, kx + 1), val(1 - sx, 0, kx),
+                               val(sx, 1, kx), val(sz, 1, kx + 1), val(1 - sx, 1, kx), Y,
+                               2 * (m - 1));
         }
         __syncthreads();
-        if (tid < 2 * cnt) {
-            const int poly = tid / cnt, kx = m + tid % cnt;
-            slot[poly][kx] ^= 1;
-        }
+        if (tid < cnt) slot[0][m + tid] ^= 1;
         __syncthreads();
     }
 
     // ---- re-interleave and recompose: w_2i = ce_i, w_2i+1 = co_(i+1) ----
     if (tid <= 2 * n) {
         const int poly = tid & 1, m = (tid + 1) >> 1;
-        terms[tid] = val(slot[poly][m], poly, m);
+        terms[tid] = val(slot[0][m], poly, m);
     }
     __syncthreads();
     block_recompose([&](long t, long x) -> u32 { return terms[t][x]; }, 2 * n + 1, Y, g.b,
@@ -566,7 +639,8 @@ interp_warp_kernel(InterpArgs a, DivTable dt, long P) {
     const LevelGeom& g = a.g;
     const int n = g.n, Y = g.Y;
     const int npts = 2 * g.B - 1;
-    u32* base = sm + (long)warp * 2 * (n + 1) * Y;
+    // values: shared memory when they fit, else this product's slice of the work buffer
+    u32* base = a.use_smem ? sm + (long)warp * 2 * (n + 1) * Y : a.work + k * (long)(2 * (n + 1)) * Y;
     auto val = [&](int poly, int m) -> u32* { return base + (long)(poly * (n + 1) + m) * Y; };
     const u32* yk = a.y + k * npts * (long)g.ystride;
     auto sgn = [&](int p) -> bool {
@@ -575,29 +649,29 @@ interp_warp_kernel(InterpArgs a, DivTable dt, long P) {
         if (a.sv) s ^= a.sv[k * npts + p] != 0;
         return s;
     };
-    chain_copy(yk, 2 * g.e, val(0, 0), Y);
-    chain_copy(nullptr, 0, val(1, 0), Y);
+    chain_copy<4>(yk, 2 * g.e, val(0, 0), Y);
+    chain_copy<4>(nullptr, 0, val(1, 0), Y);
     for (int m = 1; m <= n; ++m) {
         const u32* Pp = yk + (2 * m - 1) * (long)g.ystride;
         const u32* Mm = yk + (2 * m) * (long)g.ystride;
-        chain_even_odd(Pp, Mm, 2 * g.e, sgn(2 * m), m, val(0, m), val(1, m), Y);
+        chain_even_odd<4>(Pp, Mm, 2 * g.e, sgn(2 * m), m, val(0, m), val(1, m), Y);
     }
     __syncwarp();
     for (int kk = 1; kk <= n; ++kk)
-        for (int m = n; m >= kk; --m)
-            for (int poly = 0; poly < 2; ++poly) {
-                const int R = m == kk ? 2 * (m - 1) : 2 * (m - kk - 1);
-                const bool div = m > kk;
-                chain_sub_shr_div(val(poly, m), val(poly, m - 1), val(poly, m), Y, R,
-                                  div ? dt.d[0][kk] : dt.d[0][0], div ? dt.d[1][kk] : dt.d[1][0]);
-                __syncwarp();
-            }
+        for (int m = n; m >= kk; --m) {
+            const int R = m == kk ? 2 * (m - 1) : 2 * (m - kk - 1);
+            const bool div = m > kk;
+            chain2_sub_shr_div<4>(val(0, m), val(0, m - 1), val(0, m), val(1, m), val(1, m - 1),
+                                  val(1, m), Y, R, div ? dt.d[0][kk] : dt.d[0][0],
+                                  div ? dt.d[1][kk] : dt.d[1][0]);
+            __syncwarp();
+        }
     for (int m = n - 1; m >= 1; --m)
-        for (int kx = m; kx <= n - 1; ++kx)
-            for (int poly = 0; poly < 2; ++poly) {
-                chain_sub_shl(val(poly, kx), val(poly, kx + 1), val(poly, kx), Y, 2 * (m - 1));
-                __syncwarp();
-            }
+        for (int kx = m; kx <= n - 1; ++kx) {
+            chain2_sub_shl<4>(val(0, kx), val(0, kx + 1), val(0, kx), val(1, kx), val(1, kx + 1),
+                              val(1, kx), Y, 2 * (m - 1));
+            __syncwarp();
+        }
     // recompose: out[l] = sum_t w_t[l - t b], w_2i = ce_i, w_2i+1 = co_(i+1)
     u32* out = a.out + k * a.out_stride;
     const bool aligned = ((reinterpret_cast<uintptr_t>(out) & 15u) == 0);
@@ -635,23 +709,34 @@ interp_warp_kernel(InterpArgs a, DivTable dt, long P) {
     }
 }
 
-size_t interp_work_bytes(const LevelGeom& g) {
-    const size_t bytes = (size_t)4 * (g.n + 1) * g.Y * 4;
-    return bytes <= 160 * 1024 ? 0 : bytes;
+// Kernel choice for a level: many products -> one warp per product (values in
+// shared memory when they fit, else in the work buffer); few products -> one
+// block per product.
+static bool use_warp_kernel(const LevelGeom& g, long P) { return P >= 2048; }
+static size_t warp_values_bytes(const LevelGeom& g) { return (size_t)2 * (g.n + 1) * g.Y * 4; }
+static size_t block_values_bytes(const LevelGeom& g) { return (size_t)4 * (g.n + 1) * g.Y * 4; }
+constexpr size_t WARP_SMEM_MAX = 24 * 1024;
+constexpr size_t BLOCK_SMEM_MAX = 160 * 1024;
+
+size_t interp_work_bytes(const LevelGeom& g, long P) {
+    if (use_warp_kernel(g, P)) return warp_values_bytes(g) <= WARP_SMEM_MAX ? 0 : warp_values_bytes(g);
+    return block_values_bytes(g) <= BLOCK_SMEM_MAX ? 0 : block_values_bytes(g);
 }
 
 cudaError_t launch_interp(const LevelGeom& g, const u32* y, const uint8_t* su, const uint8_t* sv,
                           u32* out, long out_stride, int out_len, u32* work, long P,
                           cudaStream_t st) {
     if (P <= 0) return cudaSuccess;
-    static const DivTable dt = make_div_table();
-    // many small products: one warp per product
-    const size_t warp_smem = (size_t)2 * (g.n + 1) * g.Y * 4;
-    if (P >= 2048 && warp_smem <= 24 * 1024) {
+    static const DivTable dt4 = make_div_table(4), dt8 = make_div_table(8);
+    const DivTable& dt = dt4;
+    // many products: one warp per product
+    if (use_warp_kernel(g, P)) {
+        const size_t warp_smem = warp_values_bytes(g);
         InterpArgs a;
         a.g = g; a.y = y; a.su = su; a.sv = sv; a.out = out; a.out_stride = out_stride;
-        a.out_len = out_len; a.work = nullptr; a.use_smem = 1;
-        int wpb = (int)((96 * 1024) / warp_smem);
+        a.out_len = out_len; a.work = work; a.use_smem = warp_smem <= WARP_SMEM_MAX;
+        if (!a.use_smem && !work) return cudaErrorInvalidValue;
+        int wpb = a.use_smem ? (int)((96 * 1024) / warp_smem) : 4;
         if (wpb > 8) wpb = 8;
         if (wpb < 1) wpb = 1;
         static bool attr_w = false;
@@ -661,7 +746,7 @@ cudaError_t launch_interp(const LevelGeom& g, const u32* y, const uint8_t* su, c
             attr_w = true;
         }
         const long grid = (P + wpb - 1) / wpb;
-        interp_warp_kernel<<<(unsigned)grid, wpb * 32, wpb * warp_smem, st>>>(a, dt, P);
+        interp_warp_kernel<<<(unsigned)grid, wpb * 32, a.use_smem ? wpb * warp_smem : 0, st>>>(a, dt, P);
         return cudaGetLastError();
     }
     InterpArgs a;
@@ -672,20 +757,24 @@ cudaError_t launch_interp(const LevelGeom& g, const u32* y, const uint8_t* su, c
     a.out = out;
     a.out_stride = out_stride;
     a.out_len = out_len;
-    const size_t wb = interp_work_bytes(g);
+    const size_t wb = interp_work_bytes(g, P);
     a.use_smem = wb == 0;
     a.work = work;
     if (!a.use_smem && !work) return cudaErrorInvalidValue;
     const size_t smem = a.use_smem ? (size_t)4 * (g.n + 1) * g.Y * 4 : 0;
-    int warps = 2 * g.n;
+    int warps = g.n + 1;  // a warp per node pair in the widest stage (even-odd: n + 1)
     if (warps < 4) warps = 4;
-    if (warps > 32) warps = 32;
+    if (warps > 16) warps = 16;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(interp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+        cudaFuncSetAttribute(interp_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+        cudaFuncSetAttribute(interp_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
         attr_set = true;
     }
-    interp_kernel<<<(unsigned)P, warps * 32, smem, st>>>(a, dt, P);
+    if (g.K == 8)
+        interp_kernel<8><<<(unsigned)P, warps * 32, smem, st>>>(a, dt8, P);
+    else
+        interp_kernel<4><<<(unsigned)P, warps * 32, smem, st>>>(a, dt4, P);
     return cudaGetLastError();
 }
 

@@ -67,7 +67,7 @@ _SIGS = {
     "tc_toom_evaluate": (ctypes.c_int, [_sz, _sz, ctypes.c_int, _u32p, _sz, _u32p, _sz, _u8p, _vp]),
     "tc_toom_interpolate": (ctypes.c_int, [_sz, _sz, ctypes.c_int, _u32p, _sz, _u8p, _u8p, _u32p,
                                            _sz, _vp, _vp]),
-    "tc_toom_interpolate_work_bytes": (ctypes.c_size_t, [_sz, ctypes.c_int]),
+    "tc_toom_interpolate_work_bytes": (ctypes.c_size_t, [_sz, _sz, ctypes.c_int]),
     "tc_serve_submit": (ctypes.c_int, [_vp, _u32p, _sz, _u32p, _sz, _u32p,
                                        ctypes.POINTER(ctypes.c_uint64)]),
     "tc_serve_poll": (ctypes.c_int, [_vp, ctypes.c_uint64]),
@@ -269,8 +269,8 @@ def tc_toom_evaluate(U, B: int, OUT=None, SGN=None, stream=None):
     return OUT, SGN
 
 
-def tc_toom_interpolate_work_bytes(limbs: int, B: int) -> int:
-    return lib().tc_toom_interpolate_work_bytes(limbs, B)
+def tc_toom_interpolate_work_bytes(count: int, limbs: int, B: int) -> int:
+    return lib().tc_toom_interpolate_work_bytes(count, limbs, B)
 
 
 def tc_toom_interpolate(Y, limbs: int, B: int, SGN_U=None, SGN_V=None, OUT=None, work=None,
@@ -280,9 +280,9 @@ def tc_toom_interpolate(Y, limbs: int, B: int, SGN_U=None, SGN_V=None, OUT=None,
     count = Y.shape[0]
     if OUT is None:
         OUT = torch.empty((count, 2 * limbs), dtype=torch.int32, device=Y.device)
-    wb = tc_toom_interpolate_work_bytes(limbs, B)
+    wb = tc_toom_interpolate_work_bytes(count, limbs, B)
     if wb and work is None:
-        work = torch.empty(wb * count, dtype=torch.uint8, device=Y.device)
+        work = torch.empty(wb, dtype=torch.uint8, device=Y.device)
     _check(lib().tc_toom_interpolate(count, limbs, B, _ptr(Y), Y.shape[-1], _ptr(SGN_U), _ptr(SGN_V),
                                      _ptr(OUT), OUT.stride(0), _ptr(work) if wb else None,
                                      _stream(stream)), "tc_toom_interpolate")

@@ -114,7 +114,8 @@ def _oracle_level(u, v, L, B):
 
 
 INTERP_CASES = [(2, 4), (2, 1000), (3, 9), (3, 1024), (4, 100), (5, 77), (8, 515), (16, 64),
-                (16, 2055), (16, 32768), (32, 96), (32, 4000), (8, 40000)]
+                (16, 2055), (16, 32768), (32, 96), (32, 4000), (8, 40000),
+                (2, 2000), (4, 8000), (2, 9000), (32, 65536)]
 
 
 @pytest.mark.parametrize("B,L", INTERP_CASES)
@@ -255,7 +256,7 @@ def test_square_lane_kernel(tc, L):
 # ---------------------------------------------------------------- many small interpolations
 # 2048 or more products with small values select the warp-per-product kernel.
 
-@pytest.mark.parametrize("B,L", [(2, 9), (3, 100), (4, 259), (8, 130), (3, 2)])
+@pytest.mark.parametrize("B,L", [(2, 9), (3, 100), (4, 259), (8, 130), (3, 2), (4, 2000), (8, 2055)])
 def test_interpolate_many_products(tc, B, L):
     import torch
     count = 2100
@@ -282,7 +283,7 @@ def test_interpolate_many_products(tc, B, L):
 def test_uniform_batch_full_size_2e20(ctx, tc, plan):
     """The benchmark's workload shape (2^20-bit operands) at a reduced batch,
     with every level's kernels in their large-batch variants."""
-    L, count = 32768, 64
+    L, count = 32768, 72   # 72 x 31 = 2232 level-1 products: the many-product kernels
     A = np.stack([inputs.uniform(L, 2 * k) for k in range(count)])
     B = np.stack([inputs.uniform(L, 2 * k + 1) for k in range(count)])
     A[3] = 0xFFFFFFFF
