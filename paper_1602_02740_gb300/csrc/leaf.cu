@@ -117,9 +117,9 @@ leaf_kernel(const u32* __restrict__ A, long lda, const u32* __restrict__ Bm, lon
         const u32* part = sm + k * g.words + g.sa_len + g.sb_len;
         u32* out = OUT + (p0 + k) * ldo;
         const bool aligned = ((reinterpret_cast<uintptr_t>(out) & 15u) == 0);
-        SignedNorm st{0, 0};
+        UnsignedNorm st{0, 0};
         for (int base = 0; base < out_len; base += CH) {
-            i64 cols[4];
+            u64 cols[4];
 #pragma unroll
             for (int jj = 0; jj < 4; ++jj) {
                 const int c = base + 4 * lane + jj;
@@ -130,10 +130,10 @@ leaf_kernel(const u32* __restrict__ A, long lda, const u32* __restrict__ Bm, lon
                     if (x - 1 >= 0 && x - 1 < g.NW) S += part[(1 * g.RB + r) * g.NW + x - 1];
                     if (x - 2 >= 0 && x - 2 < g.NW) S += part[(2 * g.RB + r) * g.NW + x - 2];
                 }
-                cols[jj] = (i64)S;
+                cols[jj] = S;
             }
             u32 d[4];
-            warp_norm_signed(cols, st, d);
+            warp_norm_unsigned(cols, st, d);
             const int pos = base + 4 * lane;
             if (aligned && pos + 4 <= out_len) {
                 st4(out + pos, d);

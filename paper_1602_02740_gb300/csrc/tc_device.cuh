@@ -133,6 +133,49 @@ __device__ __forceinline__ void warp_norm_signed(const i64 cols[4], SignedNorm& 
     st.col_carry = __shfl_sync(FULL, c[3], 31);
 }
 
+// Normalisation of NON-NEGATIVE column sums (< 2^62): after adding each
+// column's carry to the next digit every limb is below 2^32 + 2^30, so one
+// binary carry-lookahead (generate: y >= 2^32, propagate: y = 2^32 - 1)
+// finishes the job.
+struct UnsignedNorm {
+    u64 col_carry;  // carry of the previous chunk's last column
+    u32 carry;      // 0/1 carry into this chunk
+};
+
+__device__ __forceinline__ void warp_norm_unsigned(const u64 cols[4], UnsignedNorm& st, u32 out[4]) {
+    const int lane = lane_id();
+    u64 c[4];
+    u32 d[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        d[j] = (u32)cols[j];
+        c[j] = cols[j] >> 32;
+    }
+    u64 prev_c = __shfl_up_sync(FULL, c[3], 1);
+    if (lane == 0) prev_c = st.col_carry;
+    u64 y[4];
+    y[0] = (u64)d[0] + prev_c;
+#pragma unroll
+    for (int j = 1; j < 4; ++j) y[j] = (u64)d[j] + c[j - 1];
+    bool g = false, p = true;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const bool gj = (y[j] >> 32) != 0, pj = y[j] == 0xffffffffull;
+        g = gj || (pj && g);
+        p = pj && p;
+    }
+    u32 cout;
+    u32 x = warp_carry_scan(g, p, st.carry, &cout);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const u64 v = y[j] + x;
+        out[j] = (u32)v;
+        x = (u32)(v >> 32);
+    }
+    st.carry = cout;
+    st.col_carry = __shfl_sync(FULL, c[3], 31);
+}
+
 // ---------------------------------------------------------------------------
 // Exact division by an odd constant d < 2^31 (multiply by d^-1 mod 2^32, the
 // Jebelean / Granlund-Montgomery exact division), chunk-parallel.

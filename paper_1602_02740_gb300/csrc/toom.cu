@@ -59,25 +59,51 @@ __device__ __forceinline__ void eval_cols(const u32* row, int s, int B, int b, i
     O = (i64)o;
 }
 
+struct EvalCarry {
+    u32 plus;   // carry of E + O into this chunk
+    u32 minus;  // borrow of |E - O| into this chunk
+};
+
+// Column sums e, o (non-negative) of one chunk -> digits of U(x) = E + O and
+// of |U(-x)| = sign (E - O).  E and O are normalised on their own, then added
+// and subtracted with carry/borrow scans.
+__device__ __forceinline__ void eval_finish(const u64 e[4], const u64 o[4], int sign,
+                                            UnsignedNorm& ne, UnsignedNorm& no, EvalCarry& cpm,
+                                            u32 dp[4], u32 dm[4]) {
+    u32 E[4], O[4];
+    warp_norm_unsigned(e, ne, E);
+    warp_norm_unsigned(o, no, O);
+    warp_add_seg<4>(E, O, cpm.plus, dp);
+    if (sign > 0) warp_sub_seg<4>(E, O, cpm.minus, dm);
+    else warp_sub_seg<4>(O, E, cpm.minus, dm);
+}
+
+// Padded shared-memory index: one spare word per 32 makes the lane pattern
+// 4t + c conflict-free.
+__host__ __device__ __forceinline__ int pad32(int x) { return x + (x >> 5); }
+
 __global__ void __launch_bounds__(1024)
 eval_kernel(const u32* __restrict__ in, long in_stride, LevelGeom g, u32* __restrict__ out,
             uint8_t* __restrict__ sgn, long P) {
+    extern __shared__ __align__(16) u32 win[];  // [B][pad32(CH + W)]
     const long k = blockIdx.x;
     if (k >= P) return;
     const u32* row = in + k * in_stride;
     const int npts = 2 * g.B - 1;
     u32* orow0 = out + (k * npts) * (long)g.estride;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, nt = blockDim.x;
     // point 0: U(0) = u_0
-    for (int i = tid; i < g.estride; i += blockDim.x) orow0[i] = (i < g.b && i < g.s) ? row[i] : 0u;
+    for (int i = tid; i < g.estride; i += nt) orow0[i] = (i < g.b && i < g.s) ? row[i] : 0u;
     if (tid == 0) sgn[k * npts] = 0;
 
     const int warp = tid >> 5, lane = tid & 31;
-    const int nw = blockDim.x >> 5;
-    for (int j = warp; j < g.n; j += nw) {
-        // ---- sign of E - O, top-down ----
+    const int j = warp;             // this warp evaluates x = 2^j (blockDim = 32 max(n, 1))
+    const bool has_point = j < g.n;
+    // ---- sign of E - O, top-down (global reads; almost always one window) ----
+    int sign = 1;
+    if (has_point) {
         i64 T = 0;
-        int sign = 0;
+        sign = 0;
         for (int top = g.e - 1; top >= 0 && sign == 0; top -= 32) {
             const int l = top - lane;
             i64 d = 0;
@@ -97,27 +123,150 @@ eval_kernel(const u32* __restrict__ in, long in_stride, LevelGeom g, u32* __rest
             }
         }
         if (sign == 0) sign = T < 0 ? -1 : 1;
+    }
 
-        u32* rp = out + (k * npts + 2 * j + 1) * (long)g.estride;
-        u32* rm = out + (k * npts + 2 * j + 2) * (long)g.estride;
-        SignedNorm sp{0, 0}, smn{0, 0};
-        for (int base = 0; base < g.estride; base += CH) {
-            i64 cp[4], cm[4];
+    // ---- bottom-up pass: chunks of CH output limbs staged in shared memory ----
+    const int W = ((g.n - 1) * g.n >> 5) + 1;  // halo: largest limb shift + 1
+    const int wlen = pad32(CH + W) + 1;
+    u32* rp = out + (k * npts + 2 * j + 1) * (long)g.estride;
+    u32* rm = out + (k * npts + 2 * j + 2) * (long)g.estride;
+    UnsignedNorm ne{0, 0}, no{0, 0};
+    EvalCarry cpm{0, 0};
+    for (int base = 0; base < g.estride; base += CH) {
+        __syncthreads();  // previous chunk's reads are done
+        for (int idx = tid; idx < g.B * (CH + W); idx += nt) {
+            const int i = idx / (CH + W), xo = idx - i * (CH + W);
+            const int x = base - W + xo;  // limb index within block i
+            const int gi = i * g.b + x;
+            win[i * wlen + pad32(xo)] = (x >= 0 && x < g.b && gi < g.s) ? __ldg(row + gi) : 0u;
+        }
+        __syncthreads();
+        if (has_point) {
+            u64 e[4] = {0, 0, 0, 0}, o[4] = {0, 0, 0, 0};
+            for (int i = 0; i < g.B; ++i) {
+                const int sh = j * i;
+                const int qa = sh >> 5, r = sh & 31;
+                const u32* w = win + i * wlen;
+                // limbs x = 4 lane + jj - qa - 1 .. + 0 of block i, window offset W
+                const int x0 = 4 * lane + W - qa - 1;
+                u32 v[5];
 #pragma unroll
-            for (int jj = 0; jj < 4; ++jj) {
-                const int l = base + 4 * lane + jj;
-                i64 E = 0, O = 0;
-                if (l < g.e) eval_cols(row, g.s, g.B, g.b, j, l, E, O);
-                cp[jj] = E + O;
-                cm[jj] = sign > 0 ? E - O : O - E;
+                for (int q = 0; q < 5; ++q) v[q] = w[pad32(x0 + q)];
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) {
+                    const u32 t = fshl(v[jj], v[jj + 1], (u32)r);
+                    if (i & 1) o[jj] += t; else e[jj] += t;
+                }
             }
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj)
+                if (base + 4 * lane + jj >= g.e) { e[jj] = 0; o[jj] = 0; }
             u32 dp[4], dm[4];
-            warp_norm_signed(cp, sp, dp);
-            warp_norm_signed(cm, smn, dm);
+            eval_finish(e, o, sign, ne, no, cpm, dp, dm);
             const int pos = base + 4 * lane;
             if (pos < g.estride) {  // estride is a multiple of 4
                 st4(rp + pos, dp);
                 st4(rm + pos, dm);
+            }
+        }
+    }
+    if (has_point && lane == 0) {
+        sgn[k * npts + 2 * j + 1] = 0;
+        sgn[k * npts + 2 * j + 2] = sign < 0 ? 1 : 0;
+    }
+}
+
+// Short rows: one warp per row, every point of the row, the row staged in
+// shared memory (padded layout), several rows per block, no block barriers.
+__global__ void __launch_bounds__(256)
+eval_warp_kernel(const u32* __restrict__ in, long in_stride, LevelGeom g, u32* __restrict__ out,
+                 uint8_t* __restrict__ sgn, long P, int rowlen) {
+    extern __shared__ __align__(16) u32 rows_sm[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long k = (long)blockIdx.x * (blockDim.x >> 5) + warp;
+    if (k >= P) return;  // warp-uniform
+    u32* rs = rows_sm + (long)warp * rowlen;
+    const u32* row = in + k * in_stride;
+    const int npts = 2 * g.B - 1;
+    const int W = ((g.n - 1) * g.n >> 5) + 1;
+    // staged layout: block i occupies padded slots [i (b + W), i (b + W) + b + W), first W zero
+    const int bw = g.b + W;
+    for (int x = lane; x < g.B * bw; x += 32) {
+        const int i = x / bw, xi = x - i * bw - W;
+        const int gi = i * g.b + xi;
+        rs[pad32(x)] = (xi >= 0 && gi < g.s) ? __ldg(row + gi) : 0u;
+    }
+    __syncwarp();
+    auto U = [&](int i, int x) -> u32 {  // limb x of block i (zero outside [0, b))
+        return (x < g.b) ? rs[pad32(i * bw + W + x)] : 0u;
+    };
+    u32* orow0 = out + (k * npts) * (long)g.estride;
+    for (int pos = 4 * lane; pos < g.estride; pos += CH) {
+        u32 v[4];
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) v[jj] = (pos + jj < g.b && pos + jj < g.s) ? U(0, pos + jj) : 0u;
+        st4(orow0 + pos, v);
+    }
+    if (lane == 0) sgn[k * npts] = 0;
+    for (int j = 0; j < g.n; ++j) {
+        // sign of E - O, top-down
+        i64 T = 0;
+        int sign = 0;
+        for (int top = g.e - 1; top >= 0 && sign == 0; top -= 32) {
+            const int l = top - lane;
+            i64 d = 0;
+            if (l >= 0) {
+                u64 e = 0, o = 0;
+                for (int i = 0; i < g.B; ++i) {
+                    const int sh = j * i, qa = sh >> 5, r = sh & 31;
+                    const u32 hi = (l - qa >= 0) ? U(i, l - qa) : 0u;
+                    const u32 lo = (l - qa - 1 >= 0) ? U(i, l - qa - 1) : 0u;
+                    const u32 t = fshl(lo, hi, (u32)r);
+                    if (i & 1) o += t; else e += t;
+                }
+                d = (i64)e - (i64)o;
+            }
+            const unsigned nz = __ballot_sync(FULL, d != 0);
+            if (T == 0 && nz == 0) continue;
+            for (int t = 0; t < 32; ++t) {
+                const i64 dt = __shfl_sync(FULL, d, t);
+                if (top - t < 0) break;
+                T = T * 4294967296LL + dt;
+                if (T >= 17) { sign = 1; break; }
+                if (T <= -17) { sign = -1; break; }
+            }
+        }
+        if (sign == 0) sign = T < 0 ? -1 : 1;
+        u32* rp = out + (k * npts + 2 * j + 1) * (long)g.estride;
+        u32* rm = out + (k * npts + 2 * j + 2) * (long)g.estride;
+        UnsignedNorm ne{0, 0}, no{0, 0};
+        EvalCarry cpm{0, 0};
+        for (int base = 0; base < g.estride; base += CH) {
+            u64 e[4] = {0, 0, 0, 0}, o[4] = {0, 0, 0, 0};
+            const int l0 = base + 4 * lane;
+            if (l0 < g.e) {
+                for (int i = 0; i < g.B; ++i) {
+                    const int sh = j * i, qa = sh >> 5, r = sh & 31;
+                    const int x0 = l0 - qa - 1;  // >= -W: the zero halo covers it
+                    u32 v[5];
+#pragma unroll
+                    for (int q = 0; q < 5; ++q)
+                        v[q] = (x0 + q < g.b) ? rs[pad32(i * bw + W + x0 + q)] : 0u;
+#pragma unroll
+                    for (int jj = 0; jj < 4; ++jj) {
+                        const u32 t = fshl(v[jj], v[jj + 1], (u32)r);
+                        if (i & 1) o[jj] += t; else e[jj] += t;
+                    }
+                }
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj)
+                    if (l0 + jj >= g.e) { e[jj] = 0; o[jj] = 0; }
+            }
+            u32 dp[4], dm[4];
+            eval_finish(e, o, sign, ne, no, cpm, dp, dm);
+            if (l0 < g.estride) {
+                st4(rp + l0, dp);
+                st4(rm + l0, dm);
             }
         }
         if (lane == 0) {
@@ -130,9 +279,30 @@ eval_kernel(const u32* __restrict__ in, long in_stride, LevelGeom g, u32* __rest
 cudaError_t launch_eval(const u32* in, long in_stride, const LevelGeom& g, u32* out,
                         uint8_t* sgn, long P, cudaStream_t st) {
     if (P <= 0) return cudaSuccess;
-    int warps = g.n < 1 ? 1 : g.n;
-    if (warps > 32) warps = 32;
-    eval_kernel<<<(unsigned)P, warps * 32, 0, st>>>(in, in_stride, g, out, sgn, P);
+    {
+        const int W = ((g.n - 1) * g.n >> 5) + 1;
+        const int staged = g.B * (g.b + W);
+        const int rowlen = pad32(staged) + 4;
+        if (P >= 1024 && rowlen * 4 <= 12 * 1024) {
+            static bool attr = false;
+            if (!attr) {
+                cudaFuncSetAttribute(eval_warp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     100 * 1024);
+                attr = true;
+            }
+            int wpb = (int)((48 * 1024) / ((size_t)rowlen * 4));
+            if (wpb > 8) wpb = 8;
+            if (wpb < 1) wpb = 1;
+            const long grid = (P + wpb - 1) / wpb;
+            eval_warp_kernel<<<(unsigned)grid, wpb * 32, (size_t)wpb * rowlen * 4, st>>>(
+                in, in_stride, g, out, sgn, P, rowlen);
+            return cudaGetLastError();
+        }
+    }
+    const int warps = g.n < 1 ? 1 : g.n;  // n <= 31: one warp per point pair
+    const int W = ((g.n - 1) * g.n >> 5) + 1;
+    const size_t smem = (size_t)g.B * ((CH + W) + ((CH + W) >> 5) + 1) * 4;
+    eval_kernel<<<(unsigned)P, warps * 32, smem, st>>>(in, in_stride, g, out, sgn, P);
     return cudaGetLastError();
 }
 
@@ -675,10 +845,10 @@ interp_warp_kernel(InterpArgs a, DivTable dt, long P) {
     // recompose: out[l] = sum_t w_t[l - t b], w_2i = ce_i, w_2i+1 = co_(i+1)
     u32* out = a.out + k * a.out_stride;
     const bool aligned = ((reinterpret_cast<uintptr_t>(out) & 15u) == 0);
-    SignedNorm st{0, 0};
+    UnsignedNorm st{0, 0};
     const int nterms = 2 * n + 1;
     for (int base_l = 0; base_l < a.out_len; base_l += CH) {
-        i64 cols[4];
+        u64 cols[4];
         const int l0 = base_l + 4 * lane;
         int t0 = l0 / g.b;
 #pragma unroll
@@ -695,10 +865,10 @@ interp_warp_kernel(InterpArgs a, DivTable dt, long P) {
                     S += val(t & 1, (t + 1) >> 1)[x];
                 }
             }
-            cols[j] = (i64)S;
+            cols[j] = S;
         }
         u32 d[4];
-        warp_norm_signed(cols, st, d);
+        warp_norm_unsigned(cols, st, d);
         if (aligned && l0 + 4 <= a.out_len) {
             st4(out + l0, d);
         } else {
