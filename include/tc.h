@@ -180,6 +180,33 @@ tc_status tc_toom_interpolate(size_t count, size_t limbs, int B,
  * limbs split into B blocks (0 when it runs in shared memory). */
 size_t tc_toom_interpolate_work_bytes(size_t count, size_t limbs, int B);
 
+/*
+ * Interpolation without any device allocation (the paper has no counterpart:
+ * this is an integration convenience).  For callers that must not allocate
+ * device memory while they run -- e.g. a service that reserved all GPU memory
+ * for its own pool at start-up, or a latency-critical loop where
+ * cudaMalloc/cudaFree (which may synchronise the device) is not acceptable.
+ *
+ * Computes exactly what tc_toom_interpolate computes, with the same arguments
+ * minus `work`: the scratch comes from one fixed device array of
+ * TC_NOALLOC_SCRATCH_BYTES inside the library, which every GPU that loads the
+ * library holds until the process exits.  Calls needing more scratch than
+ * that (tc_toom_interpolate_work_bytes(count, limbs, B) > TC_NOALLOC_SCRATCH_BYTES)
+ * are rejected with TC_ENOMEM before any launch; nothing is allocated, by
+ * this library or any other, on any path.  The first call that needs scratch
+ * on a device looks up the array's device address for that device (make that
+ * first call before any stream capture); later calls reuse it.
+ * Every call on a device shares the one array and it keeps the last call's
+ * contents (nothing in it needs to start at zero: each call writes all the
+ * scratch it reads).  Calls whose GPU work overlaps in time race on the
+ * array: serialise them, e.g. on one stream.
+ */
+#define TC_NOALLOC_SCRATCH_BYTES (16u << 20)
+tc_status tc_toom_interpolate_noalloc(size_t count, size_t limbs, int B,
+                                      const uint32_t *Y, size_t ystride,
+                                      const uint8_t *SGN_U, const uint8_t *SGN_V,
+                                      uint32_t *OUT, size_t ldo, void *stream);
+
 /* ---------------------------------------------------------------------
  * Serving: a request loop on a host thread that admits products while the
  * scratch budget and a slot allow, groups them by size class, and keeps the

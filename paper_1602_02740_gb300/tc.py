@@ -68,6 +68,8 @@ _SIGS = {
     "tc_toom_interpolate": (ctypes.c_int, [_sz, _sz, ctypes.c_int, _u32p, _sz, _u8p, _u8p, _u32p,
                                            _sz, _vp, _vp]),
     "tc_toom_interpolate_work_bytes": (ctypes.c_size_t, [_sz, _sz, ctypes.c_int]),
+    "tc_toom_interpolate_noalloc": (ctypes.c_int, [_sz, _sz, ctypes.c_int, _u32p, _sz, _u8p, _u8p,
+                                                   _u32p, _sz, _vp]),
     "tc_serve_submit": (ctypes.c_int, [_vp, _u32p, _sz, _u32p, _sz, _u32p,
                                        ctypes.POINTER(ctypes.c_uint64)]),
     "tc_serve_poll": (ctypes.c_int, [_vp, ctypes.c_uint64]),
@@ -286,6 +288,25 @@ def tc_toom_interpolate(Y, limbs: int, B: int, SGN_U=None, SGN_V=None, OUT=None,
     _check(lib().tc_toom_interpolate(count, limbs, B, _ptr(Y), Y.shape[-1], _ptr(SGN_U), _ptr(SGN_V),
                                      _ptr(OUT), OUT.stride(0), _ptr(work) if wb else None,
                                      _stream(stream)), "tc_toom_interpolate")
+    return OUT
+
+
+TC_NOALLOC_SCRATCH_BYTES = 16 << 20
+
+
+def tc_toom_interpolate_noalloc(Y, limbs: int, B: int, SGN_U=None, SGN_V=None, OUT=None,
+                                stream=None):
+    """tc_toom_interpolate with the library's fixed built-in scratch (no device
+    allocation by the library).  For callers that cannot allocate device memory
+    while running; the output tensor, if not given, is allocated here by torch
+    as a convenience of this binding, not by the library."""
+    import torch
+    count = Y.shape[0]
+    if OUT is None:
+        OUT = torch.empty((count, 2 * limbs), dtype=torch.int32, device=Y.device)
+    _check(lib().tc_toom_interpolate_noalloc(count, limbs, B, _ptr(Y), Y.shape[-1], _ptr(SGN_U),
+                                             _ptr(SGN_V), _ptr(OUT), OUT.stride(0),
+                                             _stream(stream)), "tc_toom_interpolate_noalloc")
     return OUT
 
 
