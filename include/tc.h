@@ -228,7 +228,8 @@ tc_status tc_serve_poll(tc_ctx *ctx, uint64_t ticket);
 tc_status tc_serve_stats(tc_ctx *ctx, double *p50_ms, double *p99_ms, double *bits_per_s,
                          uint64_t *completed);
 
-/* Stop the serving loop (pending requests complete first). */
+/* Stop the serving loop: pending requests complete first, then the loop's
+ * tickets and statistics are discarded (the next submit starts a new loop). */
 tc_status tc_serve_stop(tc_ctx *ctx);
 
 /* ---------------------------------------------------------------------

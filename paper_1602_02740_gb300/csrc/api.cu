@@ -80,15 +80,6 @@ tc_opts plan_for(tc_ctx* ctx, size_t s) {
     return default_plan(s);
 }
 
-// Scratch layout of a uniform batch.
-struct BatchLayout {
-    std::vector<LevelGeom> g;
-    std::vector<long> P;          // products at each level (P[0] = count)
-    std::vector<size_t> evalU, evalV, sgnU, sgnV, prod, work;  // byte offsets
-    size_t total = 0;
-};
-
-static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 BatchLayout layout_for(size_t count, size_t s, const tc_opts& o, bool square) {
     BatchLayout L;
@@ -403,7 +394,9 @@ __global__ void scatter_rows(const u32* src, int stride, const int64_t* off, con
         d[i] = s[i];
 }
 
-size_t size_class(size_t L) {
+}  // namespace
+
+size_t tc::size_class(size_t L) {
     // classes 2^k and 3 * 2^(k-1): at most 50% padding
     size_t c = 32;
     while (c < L) {
@@ -413,8 +406,6 @@ size_t size_class(size_t L) {
     }
     return c;
 }
-
-}  // namespace
 
 // Products listed by (offset, length) triples; all device limb buffers, host index arrays.
 static tc_status mul_general(tc_ctx* ctx, size_t count, const u32* A, const int64_t* a_off,

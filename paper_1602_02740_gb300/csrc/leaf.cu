@@ -17,6 +17,8 @@
 // Reduction.  Tiles write their column accumulators to shared memory, one
 // window of columns per row block; a warp per product then sums the row
 // blocks per output limb and resolves carries with the warp scans.
+#include <mutex>
+
 #include "tc_device.cuh"
 #include "tc_internal.h"
 
@@ -277,11 +279,10 @@ cudaError_t launch_leaf(const u32* A, long lda, const u32* Bm, long ldb, u32* OU
     int threads = tiles * ppc >= 256 ? 256 : ((tiles * ppc + 31) / 32) * 32;
     if (threads < 64) threads = 64;
     const size_t smem = (size_t)ppc * g.words * 4;
-    static bool attr_set = false;
-    if (!attr_set) {
+    static std::once_flag attr_once;
+    std::call_once(attr_once, [] {
         cudaFuncSetAttribute(leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-        attr_set = true;
-    }
+    });
     const long grid = (P + ppc - 1) / ppc;
     leaf_kernel<<<(unsigned)grid, threads, smem, st>>>(A, lda, Bm, ldb, OUT, ldo, g, P, ppc);
     return cudaGetLastError();

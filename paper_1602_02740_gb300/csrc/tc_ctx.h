@@ -8,9 +8,33 @@
 
 #include "../../include/tc.h"
 
+#include "tc_internal.h"
+
 namespace tc {
 struct Server;
 tc_opts plan_for(tc_ctx* ctx, size_t s);
+bool plan_valid(const tc_opts& o, size_t s);
+
+// Scratch layout of a uniform batch (byte offsets into one scratch block).
+struct BatchLayout {
+    std::vector<LevelGeom> g;
+    std::vector<long> P;          // products at each level (P[0] = count)
+    std::vector<size_t> evalU, evalV, sgnU, sgnV, prod, work;
+    size_t total = 0;
+};
+
+inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+BatchLayout layout_for(size_t count, size_t s, const tc_opts& o, bool square);
+
+// Run a uniform batch of `count` s x s products (operand rows A/Bm, result rows
+// OUT) with scratch `base` laid out by L.  ctx may be null (no phase timing).
+tc_status run_uniform(const BatchLayout& L, char* base, size_t count, size_t s, const uint32_t* A,
+                      long lda, const uint32_t* Bm, long ldb, uint32_t* OUT, long ldo, bool square,
+                      cudaStream_t st, tc_ctx* ctx);
+
+// Padded balanced length class of an operand length (at most 50% padding).
+size_t size_class(size_t L);
 }  // namespace tc
 
 struct tc_ctx {

@@ -7,6 +7,8 @@
 //
 // Points (Section 6): x = 0 and x = +-2^j, j = 0..n-1, stored in the order
 // 0, +1, -1, +2, -2, ...; signed values are sign-magnitude.
+#include <mutex>
+
 #include "tc_device.cuh"
 #include "tc_internal.h"
 
@@ -284,12 +286,11 @@ cudaError_t launch_eval(const u32* in, long in_stride, const LevelGeom& g, u32* 
         const int staged = g.B * (g.b + W);
         const int rowlen = pad32(staged) + 4;
         if (P >= 1024 && rowlen * 4 <= 12 * 1024) {
-            static bool attr = false;
-            if (!attr) {
+            static std::once_flag attr_once;
+            std::call_once(attr_once, [] {
                 cudaFuncSetAttribute(eval_warp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      100 * 1024);
-                attr = true;
-            }
+            });
             int wpb = (int)((48 * 1024) / ((size_t)rowlen * 4));
             if (wpb > 8) wpb = 8;
             if (wpb < 1) wpb = 1;
@@ -909,12 +910,11 @@ cudaError_t launch_interp(const LevelGeom& g, const u32* y, const uint8_t* su, c
         int wpb = a.use_smem ? (int)((96 * 1024) / warp_smem) : 4;
         if (wpb > 8) wpb = 8;
         if (wpb < 1) wpb = 1;
-        static bool attr_w = false;
-        if (!attr_w) {
+        static std::once_flag attr_once;
+        std::call_once(attr_once, [] {
             cudaFuncSetAttribute(interp_warp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  200 * 1024);
-            attr_w = true;
-        }
+        });
         const long grid = (P + wpb - 1) / wpb;
         interp_warp_kernel<<<(unsigned)grid, wpb * 32, a.use_smem ? wpb * warp_smem : 0, st>>>(a, dt, P);
         return cudaGetLastError();
@@ -935,12 +935,11 @@ cudaError_t launch_interp(const LevelGeom& g, const u32* y, const uint8_t* su, c
     int warps = g.n + 1;  // a warp per node pair in the widest stage (even-odd: n + 1)
     if (warps < 4) warps = 4;
     if (warps > 16) warps = 16;
-    static bool attr_set = false;
-    if (!attr_set) {
+    static std::once_flag attr_once;
+    std::call_once(attr_once, [] {
         cudaFuncSetAttribute(interp_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
         cudaFuncSetAttribute(interp_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-        attr_set = true;
-    }
+    });
     if (g.K == 8)
         interp_kernel<8><<<(unsigned)P, warps * 32, smem, st>>>(a, dt8, P);
     else
