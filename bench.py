@@ -52,6 +52,10 @@ def parse():
     p.add_argument("--plan", default="auto", help="comma-separated B per level, or auto")
     p.add_argument("--no-sweep", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--mixed", type=int, default=4096,
+                   help="products in the mixed-size batch measurement (0 = skip)")
+    p.add_argument("--serve", type=int, default=2000,
+                   help="requests per serving run (the full serving workload is 20000; 0 = skip)")
     return p.parse_args()
 
 
@@ -167,6 +171,94 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------- mixed batch
+
+def mixed_batch(ctx, tc, count, rank, steps=3):
+    """4096 independent products, lengths log-uniform 64..65536 limbs, 25 %
+    unbalanced (ratio uniform 1..4), all in one tc_mul_batch call per step."""
+    import torch
+    from paper_1602_02740_gb300 import inputs
+    la, lb = inputs.batch_lengths(count, seed=7 + rank)
+    a_off = np.concatenate([[0], np.cumsum(la)[:-1]]).astype(np.int64)
+    b_off = np.concatenate([[0], np.cumsum(lb)[:-1]]).astype(np.int64)
+    o_off = np.concatenate([[0], np.cumsum(la + lb)[:-1]]).astype(np.int64)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(11 + rank)
+    A = torch.randint(-2 ** 31, 2 ** 31 - 1, (int(la.sum()),), dtype=torch.int32, device="cuda", generator=g)
+    B = torch.randint(-2 ** 31, 2 ** 31 - 1, (int(lb.sum()),), dtype=torch.int32, device="cuda", generator=g)
+    O = torch.empty(int((la + lb).sum()), dtype=torch.int32, device="cuda")
+    tc.tc_mul_batch(ctx, A, a_off, la, B, b_off, lb, O, o_off)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        tc.tc_mul_batch(ctx, A, a_off, la, B, b_off, lb, O, o_off)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / steps
+    bits = 32.0 * float((la + lb).sum())
+    return {"workload": f"{count} products, lengths log-uniform 64..65536 limbs, 25% unbalanced "
+                        "(ratio 1..4), one tc_mul_batch call", "mults_per_s": count / dt,
+            "ms_per_call": dt * 1e3, "product_bits_per_s": bits / dt, "steps": steps}
+
+
+# ----------------------------------------------------------------- serving
+
+def serving(ctx, tc, count, rank):
+    """Poisson stream of multiply requests, lengths log-uniform 256..2^20 limbs,
+    admitted by a 40 GB scratch budget; first the saturated rate (all submitted
+    at once), then arrivals at 0.5x and 0.8x of it.  Latency = submit -> done."""
+    import torch
+    from paper_1602_02740_gb300 import inputs
+    sctx = tc.tc_create(torch.cuda.current_device(), budget_bytes=40 << 30)
+    _, lens = inputs.poisson_stream(count, seed=5 + rank, rate_per_s=1.0)
+    lens = lens.astype(np.int64)
+    g = inputs.rng(9 + rank)
+    pool_len = 1 << 21
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(13 + rank)
+    poolA = torch.randint(-2 ** 31, 2 ** 31 - 1, (pool_len,), dtype=torch.int32, device="cuda", generator=gen)
+    poolB = torch.randint(-2 ** 31, 2 ** 31 - 1, (pool_len,), dtype=torch.int32, device="cuda", generator=gen)
+    offs_a = (g.random(count) * (pool_len - lens)).astype(np.int64)
+    offs_b = (g.random(count) * (pool_len - lens)).astype(np.int64)
+    out_off = np.concatenate([[0], np.cumsum(2 * lens)[:-1]]).astype(np.int64)
+    OUT = torch.empty(int(2 * lens.sum()), dtype=torch.int32, device="cuda")
+    views = [(poolA[offs_a[i]:offs_a[i] + lens[i]], poolB[offs_b[i]:offs_b[i] + lens[i]],
+              OUT[out_off[i]:out_off[i] + 2 * lens[i]]) for i in range(count)]
+
+    def run(rate):
+        arrivals = None
+        if rate:
+            arrivals = np.cumsum(inputs.rng(17 + rank).exponential(1.0 / rate, size=count))
+        pending = []
+        t0 = time.perf_counter()
+        for i, (a, b, o) in enumerate(views):
+            if arrivals is not None:
+                while time.perf_counter() - t0 < arrivals[i]:
+                    pending = [k for k in pending if not tc.tc_serve_poll(sctx, k)]
+            while True:
+                k = tc.tc_serve_submit(sctx, a, b, o)
+                if k >= 0:
+                    break
+                pending = [k2 for k2 in pending if not tc.tc_serve_poll(sctx, k2)]
+            pending.append(k)
+        while pending:
+            pending = [k for k in pending if not tc.tc_serve_poll(sctx, k)]
+        wall = time.perf_counter() - t0
+        st = tc.tc_serve_stats(sctx)
+        tc.tc_serve_stop(sctx)
+        return {"requests": count, "rate_per_s": rate, "wall_s": wall,
+                "completed_per_s": count / wall, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+                "product_bits_per_s": st["bits_per_s"]}
+
+    run(None)                                    # warm-up (plans, pool)
+    sat = run(None)
+    sat_rate = sat["completed_per_s"]
+    loads = [run(f * sat_rate) for f in (0.5, 0.8)]
+    sctx.close()
+    return {"workload": "Poisson stream, balanced lengths log-uniform 256..2^20 limbs, uniform limbs, "
+                        "40 GB scratch budget", "requests_per_run": count,
+            "saturated": sat, "load_0.5": loads[0], "load_0.8": loads[1]}
+
+
 # ----------------------------------------------------------------- GPU leg
 
 def main():
@@ -191,7 +283,8 @@ def main():
             dist.barrier()
 
     L, P = args.limbs, args.batch
-    ctx = tc.tc_create(local)
+    table = os.path.join(ROOT, "paper_1602_02740_gb300", "plans_gb300.txt")
+    ctx = tc.tc_create(local, table=table if os.path.exists(table) else None)
     plan = None if args.plan == "auto" else [int(x) for x in args.plan.split(",")]
     used_plan = plan or tc.tc_plan_for(ctx, L)
 
@@ -252,12 +345,16 @@ def main():
     e2e = {"value": world * P / e2e_s, "unit": "mults/s",
            "h2d_bytes_per_step": 2 * P * L * 4, "d2h_bytes_per_step": P * 2 * L * 4}
 
-    # ---- B sweep (top-level B in {2,3,4,8,16}, best lower levels of a few) ----
+    # ---- B sweep: top-level B in {2,3,4,8,16}; lower levels = the cost model's 3 best ----
     sweep = None
     if not args.no_sweep:
-        cands = {2: [[2, 16, 8, 3], [2, 8, 8, 4]], 3: [[3, 16, 4, 3], [3, 8, 8, 3]],
-                 4: [[4, 16, 4, 3], [4, 8, 8, 3]], 8: [[8, 8, 8], [8, 16, 4]],
-                 16: [[16, 8, 3], [16, 8, 4], [16, 16]]}
+        from paper_1602_02740_gb300 import autotune
+        allc = autotune.candidates(L)
+        cands = {}
+        for Btop in (2, 3, 4, 8, 16):
+            mine = [list(p) for p in allc if p and p[0] == Btop]
+            mine.sort(key=lambda p: autotune.model_seconds(L, p, P))
+            cands[Btop] = mine[:3]
         sweep = {}
         for Btop, plans in cands.items():
             best = None
@@ -279,6 +376,9 @@ def main():
             if best:
                 sweep[str(Btop)] = {"plan": best[1], "mults_per_s": P / (best[0] / 1e3),
                                     "ns_per_product": best[0] * 1e6 / P}
+
+    mixed = mixed_batch(ctx, tc, args.mixed, rank) if args.mixed else None
+    serve = serving(ctx, tc, args.serve, rank) if args.serve else None
 
     # ---- roofline of the dominant phase ----
     pk, pk_src = peaks()
@@ -319,6 +419,7 @@ def main():
                        "limbs": L, "batch_per_gpu": P, "plan": used_plan,
                        "l2": "operands (152 MB) exceed the 129 MB L2; no flush"},
             "roofline": roof, "phases": phase_summary, "sweep": sweep,
+            "mixed_batch": mixed, "serving": serve,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
         }
         print(json.dumps(line), flush=True)
