@@ -259,6 +259,24 @@ def serving(ctx, tc, count, rank):
             "saturated": sat, "load_0.5": loads[0], "load_0.8": loads[1]}
 
 
+# ----------------------------------------------------------------- ranks
+
+def combine_ranks(value, dist, device=None):
+    """Max over ranks of a per-rank duration (every rank gets the max).
+    Products are sharded, not exchanged: this is the only collective."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def rank_seed(rank: int, k: int) -> int:
+    """Seed of operand k on a rank: every rank multiplies its own products."""
+    return 1_000_000 * rank + k
+
+
 # ----------------------------------------------------------------- GPU leg
 
 def main():
@@ -292,8 +310,8 @@ def main():
     A = np.empty((P, L), dtype=np.uint32)
     B = np.empty((P, L), dtype=np.uint32)
     for k in range(P):
-        A[k] = inputs.uniform(L, 1_000_000 * rank + 2 * k)
-        B[k] = inputs.uniform(L, 1_000_000 * rank + 2 * k + 1)
+        A[k] = inputs.uniform(L, rank_seed(rank, 2 * k))
+        B[k] = inputs.uniform(L, rank_seed(rank, 2 * k + 1))
     dA, dB = tc.to_device(A), tc.to_device(B)
     dO = torch.empty((P, 2 * L), dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
@@ -319,10 +337,7 @@ def main():
     phases = tc.tc_profile_read(ctx)
     tc.tc_profile_enable(ctx, False)
     clk = clocks.stop()
-    if dist is not None:
-        t = torch.tensor([ms_total], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = combine_ranks(ms_total, dist, device="cuda")
     ms_step = ms_total / args.steps
     value = world * P / (ms_step / 1e3)
     launches = sum(p["launches"] for p in phases)
@@ -338,10 +353,7 @@ def main():
     for _ in range(e2e_steps):
         tc.tc_mul_uniform_host(ctx, hA, hB, hO, plan=used_plan)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = combine_ranks(e2e_s, dist, device="cuda")
     e2e = {"value": world * P / e2e_s, "unit": "mults/s",
            "h2d_bytes_per_step": 2 * P * L * 4, "d2h_bytes_per_step": P * 2 * L * 4}
 

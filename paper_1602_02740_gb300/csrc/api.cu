@@ -69,7 +69,7 @@ bool plan_valid(const tc_opts& o, size_t s) {
         LevelGeom g = make_level((int)L, o.B[l]);
         L = (size_t)g.e;
     }
-    return L <= (size_t)LEAF_MAX;
+    return o.levels == 0 || L <= (size_t)LEAF_MAX;  // no levels: plain schoolbook, any length
 }
 
 tc_opts plan_for(tc_ctx* ctx, size_t s) {
@@ -101,6 +101,10 @@ BatchLayout layout_for(size_t count, size_t s, const tc_opts& o, bool square) {
         sl = g.e;
     }
     L.P.push_back(P);
+    if (o.levels == 0 && s > (size_t)LEAF_MAX) {  // column buffer of the large schoolbook
+        L.work.push_back(off);
+        off = align256(off + schoolbook_big_bytes((int)s, (long)count));
+    }
     L.total = off;
     return L;
 }
@@ -164,7 +168,11 @@ tc_status run_uniform(const BatchLayout& L, char* base, size_t count, size_t s, 
     const int D = (int)L.g.size();
     if (D == 0) {
         pt.begin(1, 0, 4.0 * count * 4 * s, (double)count * s * s);
-        CK(launch_leaf(A, lda, square ? A : Bm, square ? lda : ldb, OUT, ldo, (int)s, (long)count, st));
+        if (s > (size_t)LEAF_MAX)
+            CK(launch_schoolbook_big(A, lda, square ? A : Bm, square ? lda : ldb, OUT, ldo, (int)s,
+                                     (long)count, reinterpret_cast<u32*>(base + L.work[0]), st));
+        else
+            CK(launch_leaf(A, lda, square ? A : Bm, square ? lda : ldb, OUT, ldo, (int)s, (long)count, st));
         pt.end();
         return TC_OK;
     }

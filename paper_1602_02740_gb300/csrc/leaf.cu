@@ -253,6 +253,121 @@ leaf_lane_kernel(const u32* __restrict__ A, long lda, const u32* __restrict__ Bm
     }
 }
 
+// ---------------------------------------------------------------------------
+// Plain schoolbook for operands of any length (the comparison path).
+//
+// A block owns 1024 consecutive output columns of one product and walks every
+// row that reaches them, 256 rows at a time: the 256 limbs of a and the
+// matching 1284-limb window of b are staged in shared memory and each thread
+// accumulates its 4 columns with the same 4 x 4 Comba step as the tile kernel.
+// The 96-bit column sums go to a column buffer; one block per product then
+// folds them into limbs with a block-wide carry scan.
+// ---------------------------------------------------------------------------
+constexpr int BIG_COLS = 1024, BIG_ROWS = 256;
+
+__global__ void __launch_bounds__(256)
+bigmul_columns_kernel(const u32* __restrict__ A, long lda, const u32* __restrict__ Bm, long ldb,
+                      u32* __restrict__ cols, int s, int ctiles) {
+    __shared__ __align__(16) u32 sa[BIG_ROWS];
+    __shared__ __align__(16) u32 sb[BIG_COLS + BIG_ROWS + 8];
+    const long p = blockIdx.x / ctiles;
+    const int ct = blockIdx.x - (int)(p * ctiles);
+    const int c0 = ct * BIG_COLS;
+    const u32* a = A + p * lda;
+    const u32* b = Bm + p * ldb;
+    const int t = threadIdx.x;
+    int ilo = c0 - s + 1;
+    if (ilo < 0) ilo = 0;
+    ilo = ilo / BIG_ROWS * BIG_ROWS;
+    const int ihi = c0 + BIG_COLS < s ? c0 + BIG_COLS : s;
+    u32 lo[4] = {0, 0, 0, 0}, mid[4] = {0, 0, 0, 0}, hi[4] = {0, 0, 0, 0};
+    for (int i0 = ilo; i0 < ihi; i0 += BIG_ROWS) {
+        __syncthreads();
+        const int jb = c0 - i0 - BIG_ROWS;  // sb[x] = b[jb + x]
+        for (int x = t; x < BIG_ROWS; x += blockDim.x) sa[x] = i0 + x < s ? a[i0 + x] : 0u;
+        for (int x = t; x < BIG_COLS + BIG_ROWS + 8; x += blockDim.x) {
+            const int j = jb + x;
+            sb[x] = (j >= 0 && j < s) ? b[j] : 0u;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int grp = 0; grp < BIG_ROWS / 4; ++grp) {
+            const uint4 av = *reinterpret_cast<const uint4*>(sa + 4 * grp);
+            const int xb = BIG_ROWS + 4 * t - 4 * grp - 4;
+            const uint4 b0 = *reinterpret_cast<const uint4*>(sb + xb);
+            const uint4 b1 = *reinterpret_cast<const uint4*>(sb + xb + 4);
+            const u32 a4[4] = {av.x, av.y, av.z, av.w};
+            const u32 b8[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int rho = 0; rho < 4; ++rho)
+#pragma unroll
+                for (int w = 0; w < 4; ++w) mac96(lo[w], mid[w], hi[w], a4[rho], b8[4 + w - rho]);
+        }
+    }
+    const long ncol = 2L * s;
+    u32* cl = cols + p * 3 * ncol;
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+        const long c = c0 + 4 * t + w;
+        if (c < ncol) {
+            cl[c] = lo[w];
+            cl[ncol + c] = mid[w];
+            cl[2 * ncol + c] = hi[w];
+        }
+    }
+}
+
+__global__ void __launch_bounds__(1024)
+bigmul_normalise_kernel(const u32* __restrict__ cols, u32* __restrict__ OUT, long ldo, int s) {
+    __shared__ __align__(16) u32 shscan[2 * 1024 + 80];
+    const long p = blockIdx.x;
+    const long ncol = 2L * s;
+    const u32* lo = cols + p * 3 * ncol;
+    const u32* mid = lo + ncol;
+    const u32* hi = mid + ncol;
+    u32* out = OUT + p * ldo;
+    const bool aligned = ((reinterpret_cast<uintptr_t>(out) & 15u) == 0);
+    BlockNormState st{0, 0};
+    const long chunk = 4L * blockDim.x;
+    for (long base = 0; base < ncol; base += chunk) {
+        u64 cs[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const long c = base + 4L * threadIdx.x + j;
+            u64 v = 0;
+            if (c < ncol) {
+                v = lo[c];
+                if (c >= 1) v += mid[c - 1];
+                if (c >= 2) v += hi[c - 2];
+            }
+            cs[j] = v;
+        }
+        u32 d[4];
+        block_norm_unsigned(cs, st, d, shscan);
+        const long pos = base + 4L * threadIdx.x;
+        if (aligned && pos + 4 <= ncol) {
+            st4(out + pos, d);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (pos + j < ncol) out[pos + j] = d[j];
+        }
+    }
+}
+
+size_t schoolbook_big_bytes(int s, long P) { return (size_t)P * 3 * 2 * (size_t)s * 4; }
+
+cudaError_t launch_schoolbook_big(const u32* A, long lda, const u32* Bm, long ldb, u32* OUT,
+                                  long ldo, int s, long P, u32* cols, cudaStream_t st) {
+    if (P <= 0) return cudaSuccess;
+    const int ctiles = (2 * s + BIG_COLS - 1) / BIG_COLS;
+    bigmul_columns_kernel<<<(unsigned)(P * ctiles), BIG_COLS / 4, 0, st>>>(A, lda, Bm, ldb, cols, s, ctiles);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    bigmul_normalise_kernel<<<(unsigned)P, 1024, 0, st>>>(cols, OUT, ldo, s);
+    return cudaGetLastError();
+}
+
 // Products at or above this count use the lane-per-product kernel.
 constexpr long LANE_KERNEL_MIN = 4096;
 

@@ -29,6 +29,12 @@ constexpr int LEAF_MAX = 1024;
 cudaError_t launch_leaf(const uint32_t* A, long lda, const uint32_t* Bm, long ldb,
                         uint32_t* OUT, long ldo, int s, long P, cudaStream_t st);
 
+// Plain schoolbook of any operand length (column sums in `cols`, see below).
+size_t schoolbook_big_bytes(int s, long P);
+cudaError_t launch_schoolbook_big(const uint32_t* A, long lda, const uint32_t* Bm, long ldb,
+                                  uint32_t* OUT, long ldo, int s, long P, uint32_t* cols,
+                                  cudaStream_t st);
+
 cudaError_t launch_eval(const uint32_t* in, long in_stride, const LevelGeom& g,
                         uint32_t* out, uint8_t* sgn, long P, cudaStream_t st);
 

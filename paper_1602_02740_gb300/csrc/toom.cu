@@ -595,68 +595,6 @@ __device__ void chain_copy(const u32* src, int len, u32* dst, int Y) {
     }
 }
 
-// ---------------------------------------------------------------------------
-// Block-wide normalisation of non-negative column sums (recomposition).
-// ---------------------------------------------------------------------------
-struct BlockNormState {
-    u64 col_carry;  // carry of the previous chunk's last column
-    u32 carry;      // resolved 0/1 carry into this chunk
-};
-
-// cols: this thread's 4 column sums (each < 2^62).  sh: >= 2*warps+... words of shared scratch.
-__device__ void block_norm_unsigned(const u64 cols[4], BlockNormState& st, u32 out[4], u32* sh) {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-    u64* sh_c = reinterpret_cast<u64*>(sh);           // [blockDim] last-column carries
-    u32* sh_gp = sh + 2 * blockDim.x;                 // [nw] warp g/p bits, then [nw] warp carries
-    u32 d[4];
-    u64 c[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) { d[j] = (u32)cols[j]; c[j] = cols[j] >> 32; }
-    sh_c[tid] = c[3];
-    __syncthreads();
-    const u64 prev_c = tid == 0 ? st.col_carry : sh_c[tid - 1];
-    u64 y[4];
-    y[0] = (u64)d[0] + prev_c;
-#pragma unroll
-    for (int j = 1; j < 4; ++j) y[j] = (u64)d[j] + c[j - 1];
-    // per-limb generate (y >= 2^32) / propagate (y == 2^32 - 1), composed low to high
-    bool g = false, p = true;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const bool gj = y[j] >> 32, pj = y[j] == 0xffffffffull;
-        g = gj || (pj && g);
-        p = pj && p;
-    }
-    u32 wout;
-    warp_carry_scan(g, p, 0u, &wout);                 // warp aggregate with carry-in 0
-    const bool wp = __ballot_sync(FULL, p) == FULL;
-    if (lane == 0) sh_gp[warp] = (wout ? 1u : 0u) | (wp ? 2u : 0u);
-    const u64 last_c = sh_c[blockDim.x - 1];
-    __syncthreads();
-    if (warp == 0) {
-        // lanes past the last warp pass the carry through so lane 31 reports the block's carry
-        const u32 v = lane < nw ? sh_gp[lane] : 2u;
-        u32 bout;
-        const u32 cin = warp_carry_scan((v & 1u) != 0, (v & 2u) != 0, st.carry, &bout);
-        if (lane < nw) sh_gp[nw + lane] = cin;
-        if (lane == 0) sh_gp[2 * nw] = bout;
-    }
-    __syncthreads();
-    const u32 wcin = sh_gp[nw + warp];
-    u32 dummy;
-    u32 x = warp_carry_scan(g, p, wcin, &dummy);
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const u64 v = y[j] + x;
-        out[j] = (u32)v;
-        x = (u32)(v >> 32);
-    }
-    const u32 new_carry = sh_gp[2 * nw];
-    __syncthreads();
-    st.carry = new_carry;
-    st.col_carry = last_c;
-}
-
 // out[0..out_len) = sum over terms t < nterms of term_t shifted by t * bstep limbs,
 // where term t has Y limbs and get(t, x) returns its limb x (0 <= x < Y).
 template <class Get>

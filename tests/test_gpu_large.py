@@ -1,0 +1,69 @@
+"""Large single products: 2^24, 2^26 and 2^27-bit operands, top-level B = 16
+and 32 with recursive Toom-Cook below, and squaring at the same sizes.
+
+At these sizes the oracle checks properties that hold at any size: the
+product modulo three 61-bit primes, and the exact low 4096 limbs, which only
+depend on the low 4096 limbs of each operand (computed by the oracle's own
+product of those parts)."""
+import numpy as np
+import pytest
+
+from oracle import residues
+from oracle.limbs import from_int, to_int
+from paper_1602_02740_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+LOW = 4096
+
+CASES = [
+    (1 << 19, [16, 12, 5, 3]), (1 << 19, [32, 8, 5, 3]),
+    (1 << 21, [16, 16, 12, 5]), (1 << 21, [32, 16, 8, 4]),
+    (1 << 22, [16, 16, 16, 8]), (1 << 22, [32, 16, 12, 5]), (1 << 22, None),
+]
+
+
+def _check(a, b, out):
+    assert len(out) == len(a) + len(b)
+    assert residues.product_residues_match(a, b, out)
+    low = (to_int(a[:LOW]) * to_int(b[:LOW])) % (1 << (32 * LOW))
+    assert np.array_equal(out[:LOW], from_int(low, LOW))
+
+
+@pytest.fixture(scope="module")
+def ctx(tc):
+    c = tc.tc.tc_create(0)
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("L,plan", CASES)
+def test_large_product(ctx, tc, L, plan):
+    t = tc.tc
+    a = inputs.uniform(L, L + 3)
+    b = inputs.uniform(L, L + 4)
+    out = t.to_numpy(t.tc_mul(ctx, t.to_device(a), t.to_device(b), plan=plan))
+    _check(a, b, out)
+
+
+@pytest.mark.parametrize("L,plan", [(1 << 19, [16, 12, 5, 3]), (1 << 21, [32, 16, 8, 4]),
+                                    (1 << 22, [16, 16, 16, 8])])
+def test_large_square(ctx, tc, L, plan):
+    t = tc.tc
+    a = inputs.uniform(L, L + 5)
+    da = t.to_device(a)
+    out = t.to_numpy(t.tc_sqr(ctx, da, plan=plan))
+    _check(a, a, out)
+
+
+def test_large_all_ones_square(ctx, tc):
+    # (2^(32L) - 1)^2 = 2^(64L) - 2^(32L+1) + 1, exactly
+    t = tc.tc
+    L = 1 << 19
+    a = inputs.all_ones(L)
+    out = t.to_numpy(t.tc_sqr(ctx, t.to_device(a), plan=[16, 12, 5, 3]))
+    want = np.zeros(2 * L, dtype=np.uint32)
+    want[0] = 1
+    want[L] = 0xFFFFFFFE
+    want[L + 1:] = 0xFFFFFFFF
+    assert np.array_equal(out, want)

@@ -293,3 +293,22 @@ def test_uniform_batch_full_size_2e20(ctx, tc, plan):
         assert same_limbs(OUT[k], to_int(A[k]) * to_int(B[k])), (plan, k)
     for k in range(count):
         assert residues.product_residues_match(A[k], B[k], OUT[k]), (plan, k)
+
+
+# ---------------------------------------------------------------- plain schoolbook, any length
+
+@pytest.mark.parametrize("L", [1025, 2000, 5000, 12345])
+def test_plain_schoolbook_plan_any_length(ctx, tc, L):
+    a = inputs.uniform(L, 3 * L)
+    b = inputs.all_ones(L) if L == 2000 else inputs.uniform(L, 3 * L + 1)
+    out = host(tc.tc.tc_mul(ctx, dev(a), dev(b), plan=[]))
+    assert same_limbs(out, native.schoolbook(a, b) if L <= 5000 else to_int(a) * to_int(b))
+
+
+def test_plain_schoolbook_plan_batch(ctx, tc):
+    L, count = 3000, 7
+    A = np.stack([inputs.uniform(L, 40 + k) for k in range(count)])
+    B = np.stack([inputs.uniform(L, 80 + k) for k in range(count)])
+    OUT = host(tc.tc.tc_mul_uniform(ctx, dev(A), dev(B), plan=[]))
+    for k in range(count):
+        assert same_limbs(OUT[k], native.schoolbook(A[k], B[k]))
