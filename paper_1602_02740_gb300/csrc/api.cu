@@ -229,6 +229,17 @@ tc_status run_uniform(const BatchLayout& L, char* base, size_t count, size_t s, 
                          2 * g.s, work, L.P[l], st));
         pt.end();
     }
+    // segment-parallel levels: report a bounded wait that gave up (never expected)
+    if (ctx) {
+        for (int l = 0; l < D; ++l) {
+            if (!use_wide(L.g[l], L.P[l])) continue;
+            int flag = 0;
+            CK(cudaMemcpyAsync(&flag, wide_error_word(base + L.work[l], L.g[l], L.P[l]), sizeof(int),
+                               cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            if (flag) return TC_ETIMEOUT;
+        }
+    }
     return TC_OK;
 }
 

@@ -45,6 +45,14 @@ cudaError_t launch_interp(const LevelGeom& g, const uint32_t* y, const uint8_t* 
                           const uint8_t* sv, uint32_t* out, long out_stride, int out_len,
                           uint32_t* work, long P, cudaStream_t st);
 
+// Levels with few, huge products: segment-parallel interpolation (wide.cu).
+bool use_wide(const LevelGeom& g, long P);
+size_t wide_work_bytes(const LevelGeom& g, long P);
+int* wide_error_word(void* work, const LevelGeom& g, long P);
+cudaError_t launch_wide_interp(const LevelGeom& g, const uint32_t* y, const uint8_t* su,
+                               const uint8_t* sv, uint32_t* out, long out_stride, int out_len,
+                               void* work, long P, cudaStream_t st);
+
 // out[0 .. out_len) = sum_k w_k 2^(32 off k), w_k = rows[k*row_stride .. + row_len),
 // for `count` terms; one output (single CTA).  Used to add sliced partial products.
 cudaError_t launch_overlap_add(const uint32_t* rows, long row_stride, int row_len, long count,

@@ -828,6 +828,7 @@ constexpr size_t WARP_SMEM_MAX = 24 * 1024;
 constexpr size_t BLOCK_SMEM_MAX = 160 * 1024;
 
 size_t interp_work_bytes(const LevelGeom& g, long P) {
+    if (use_wide(g, P)) return (wide_work_bytes(g, P) + P - 1) / P;  // per product, rounded up
     if (use_warp_kernel(g, P)) return warp_values_bytes(g) <= WARP_SMEM_MAX ? 0 : warp_values_bytes(g);
     return block_values_bytes(g) <= BLOCK_SMEM_MAX ? 0 : block_values_bytes(g);
 }
@@ -836,6 +837,10 @@ cudaError_t launch_interp(const LevelGeom& g, const u32* y, const uint8_t* su, c
                           u32* out, long out_stride, int out_len, u32* work, long P,
                           cudaStream_t st) {
     if (P <= 0) return cudaSuccess;
+    if (use_wide(g, P)) {
+        if (!work) return cudaErrorInvalidValue;
+        return launch_wide_interp(g, y, su, sv, out, out_stride, out_len, work, P, st);
+    }
     static const DivTable dt4 = make_div_table(4), dt8 = make_div_table(8);
     const DivTable& dt = dt4;
     // many products: one warp per product

@@ -115,7 +115,9 @@ def _oracle_level(u, v, L, B):
 
 INTERP_CASES = [(2, 4), (2, 1000), (3, 9), (3, 1024), (4, 100), (5, 77), (8, 515), (16, 64),
                 (16, 2055), (16, 32768), (32, 96), (32, 4000), (8, 40000),
-                (2, 2000), (4, 8000), (2, 9000), (32, 65536)]
+                (2, 2000), (4, 8000), (2, 9000), (32, 65536),
+                # few long values: the segment-parallel (look-back) path
+                (3, 30000), (16, 150000), (32, 300000)]
 
 
 @pytest.mark.parametrize("B,L", INTERP_CASES)
