@@ -97,6 +97,8 @@ BatchLayout layout_for(size_t count, size_t s, const tc_opts& o, bool square) {
         L.sgnV.push_back(off); if (!square) off = align256(off + (size_t)Pn);
         L.prod.push_back(off); off = align256(off + (size_t)Pn * g.ystride * 4);
         L.work.push_back(off); off = align256(off + (size_t)P * interp_work_bytes(g, P));
+        L.evwork.push_back(off);
+        if (use_wide_eval(g, P)) off = align256(off + wide_eval_work_bytes(g, P));
         P = Pn;
         sl = g.e;
     }
@@ -186,7 +188,8 @@ tc_status run_uniform(const BatchLayout& L, char* base, size_t count, size_t s, 
         const double eval_bytes = 4.0 * L.P[l] * (g.s + (2.0 * g.B - 1) * g.estride) +
                                   (2.0 * g.B - 1) * L.P[l];
         pt.begin(0, l, eval_bytes, 0);
-        CK(launch_eval(inU, strU, g, eU, sU, L.P[l], st));
+        void* evw = base + L.evwork[l];
+        CK(launch_eval(inU, strU, g, eU, sU, L.P[l], evw, st));
         pt.end();
         inU = eU;
         strU = g.estride;
@@ -194,7 +197,7 @@ tc_status run_uniform(const BatchLayout& L, char* base, size_t count, size_t s, 
             u32* eV = reinterpret_cast<u32*>(base + L.evalV[l]);
             uint8_t* sV = reinterpret_cast<uint8_t*>(base + L.sgnV[l]);
             pt.begin(0, l, eval_bytes, 0);
-            CK(launch_eval(inV, strV, g, eV, sV, L.P[l], st));
+            CK(launch_eval(inV, strV, g, eV, sV, L.P[l], evw, st));
             pt.end();
             inV = eV;
             strV = g.estride;
@@ -232,12 +235,17 @@ tc_status run_uniform(const BatchLayout& L, char* base, size_t count, size_t s, 
     // segment-parallel levels: report a bounded wait that gave up (never expected)
     if (ctx) {
         for (int l = 0; l < D; ++l) {
-            if (!use_wide(L.g[l], L.P[l])) continue;
-            int flag = 0;
-            CK(cudaMemcpyAsync(&flag, wide_error_word(base + L.work[l], L.g[l], L.P[l]), sizeof(int),
-                               cudaMemcpyDeviceToHost, st));
-            CK(cudaStreamSynchronize(st));
-            if (flag) return TC_ETIMEOUT;
+            int* words[2] = {nullptr, nullptr};
+            if (use_wide(L.g[l], L.P[l])) words[0] = wide_error_word(base + L.work[l], L.g[l], L.P[l]);
+            if (use_wide_eval(L.g[l], L.P[l]))
+                words[1] = wide_eval_error_word(base + L.evwork[l], L.g[l], L.P[l]);
+            for (int* w : words) {
+                if (!w) continue;
+                int flag = 0;
+                CK(cudaMemcpyAsync(&flag, w, sizeof(int), cudaMemcpyDeviceToHost, st));
+                CK(cudaStreamSynchronize(st));
+                if (flag) return TC_ETIMEOUT;
+            }
         }
     }
     return TC_OK;
@@ -597,7 +605,7 @@ extern "C" tc_status tc_toom_evaluate(size_t count, size_t limbs, int B, const u
     if (estride < (size_t)g.e || estride % 4) return TC_EINVAL;
     if (count > 1 && ld < limbs) return TC_EINVAL;
     g.estride = (int)estride;
-    CK(launch_eval(U, (long)ld, g, OUT, SGN, (long)count, (cudaStream_t)stream));
+    CK(launch_eval(U, (long)ld, g, OUT, SGN, (long)count, nullptr, (cudaStream_t)stream));
     return TC_OK;
 }
 

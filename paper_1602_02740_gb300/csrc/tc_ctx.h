@@ -19,7 +19,7 @@ bool plan_valid(const tc_opts& o, size_t s);
 struct BatchLayout {
     std::vector<LevelGeom> g;
     std::vector<long> P;          // products at each level (P[0] = count)
-    std::vector<size_t> evalU, evalV, sgnU, sgnV, prod, work;
+    std::vector<size_t> evalU, evalV, sgnU, sgnV, prod, work, evwork;
     size_t total = 0;
 };
 

@@ -35,8 +35,14 @@ cudaError_t launch_schoolbook_big(const uint32_t* A, long lda, const uint32_t* B
                                   uint32_t* OUT, long ldo, int s, long P, uint32_t* cols,
                                   cudaStream_t st);
 
+// `work`: wide_eval_work_bytes(g, P) bytes when use_wide_eval(g, P), else unused.
 cudaError_t launch_eval(const uint32_t* in, long in_stride, const LevelGeom& g,
-                        uint32_t* out, uint8_t* sgn, long P, cudaStream_t st);
+                        uint32_t* out, uint8_t* sgn, long P, void* work, cudaStream_t st);
+bool use_wide_eval(const LevelGeom& g, long P);
+size_t wide_eval_work_bytes(const LevelGeom& g, long P);
+int* wide_eval_error_word(void* work, const LevelGeom& g, long P);
+cudaError_t launch_wide_eval(const uint32_t* in, long in_stride, const LevelGeom& g, uint32_t* out,
+                             uint8_t* sgn, long P, void* work, cudaStream_t st);
 
 // Per-product bytes of global work the interpolation of P products needs (0 = shared memory).
 size_t interp_work_bytes(const LevelGeom& g, long P);

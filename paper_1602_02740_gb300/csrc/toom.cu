@@ -279,8 +279,10 @@ eval_warp_kernel(const u32* __restrict__ in, long in_stride, LevelGeom g, u32* _
 }
 
 cudaError_t launch_eval(const u32* in, long in_stride, const LevelGeom& g, u32* out,
-                        uint8_t* sgn, long P, cudaStream_t st) {
+                        uint8_t* sgn, long P, void* work, cudaStream_t st) {
     if (P <= 0) return cudaSuccess;
+    // few huge rows with scratch available: segment-parallel evaluation
+    if (use_wide_eval(g, P) && work) return launch_wide_eval(in, in_stride, g, out, sgn, P, work, st);
     {
         const int W = ((g.n - 1) * g.n >> 5) + 1;
         const int staged = g.B * (g.b + W);

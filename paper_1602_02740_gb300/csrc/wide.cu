@@ -37,6 +37,9 @@ struct WideChain {
     int lenX, lenZ;   // valid limbs (zero beyond)
     int op;           // add/sub: 0 add, 1 subtract; div: divisor index k (0 = none)
     int shift;        // add/sub: left shift of Z (< 64); div: right shift of X (< 64)
+    int lenO;         // limbs written (multiple of 4); 0 = the pass's Y
+    const uint8_t* swap;  // add/sub: per-product flag (stride sSwap): exchange X and Z
+    long sSwap;
 };
 
 struct WidePass {
@@ -124,10 +127,16 @@ wide_addsub_kernel(WidePass wp, u64* status, int* counter, int* err) {
         const long rem = t - (long)seg * wp.P * wp.nch;
         const long p = rem / wp.nch;
         const int c = (int)(rem - p * wp.nch);
-        const WideChain& C = wp.ch[c];
+        WideChain C = wp.ch[c];
+        if (C.swap && C.swap[p * C.sSwap]) {  // operands exchanged for this product
+            const u32* tX = C.X; C.X = C.Z; C.Z = tX;
+            const long ts = C.sX; C.sX = C.sZ; C.sZ = ts;
+            const int tl = C.lenX; C.lenX = C.lenZ; C.lenZ = tl;
+        }
         const u32* X = C.X + p * C.sX;
         const u32* Z = C.Z + p * C.sZ;
         u32* O = C.O + p * C.sO;
+        const int lenO = C.lenO ? C.lenO : wp.Y;
         u64* st = status + (p * wp.nch + c) * wp.nseg;
         const int start = seg * WSEG;
         const int end = min(start + WSEG, wp.Y);
@@ -154,7 +163,8 @@ wide_addsub_kernel(WidePass wp, u64* status, int* counter, int* err) {
         carry = cin;
         for (int pos = start; pos < end; pos += CH) {
             addsub_chunk(C, X, Z, pos, carry, r, same);
-            st4(O + pos + 4 * lane_id(), r);
+            const int l0 = pos + 4 * lane_id();
+            if (l0 < lenO) st4(O + l0, r);
         }
     }
 }
@@ -344,90 +354,181 @@ __device__ __forceinline__ void rec_compose(u32& q, u32& T, u32 q1, u32 T1) {
     T = nT;
 }
 
-__device__ __forceinline__ void rec_chunk(const RecArgs& a, long p, int pos, UnsignedNorm& st, u32 d[4]) {
-    u64 cols[4];
+// One segment-parallel column-normalisation task: out = digits of
+// sum_l col(l) 2^(32 l) over [start, end), with the small-integer carry map
+// look-back.  col(l) returns the (non-negative) column sum at limb l.
+template <class ColFn>
+__device__ void colnorm_task(ColFn col, u64* st, int seg, int start, int end, int out_len,
+                             u32* out, int* err) {
+    const int lane = lane_id();
+    UnsignedNorm ns{0, 0};
+    u32 d[4];
+    u32 d0 = 0;
+    bool rest_ones = true;
+    for (int pos = start; pos < end; pos += CH) {
+        u64 cols[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const int l = pos + 4 * lane_id() + j;
-        u64 S = 0;
-        if (l < a.out_len) {
-            int t = l / a.b;
-            if (t > a.nterms - 1) t = a.nterms - 1;
-            for (; t >= 0; --t) {
-                const int x = l - t * a.b;
-                if (x >= a.Y) break;
-                S += a.w[t][p * a.Y + x];
-            }
+        for (int j = 0; j < 4; ++j) cols[j] = col(pos + 4 * lane + j);
+        warp_norm_unsigned(cols, ns, d);
+        const int l0 = pos + 4 * lane;
+        bool ok = true;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int l = l0 + j;
+            if (l == start) d0 = d[j];
+            else if (l < out_len && d[j] != FULL) ok = false;
         }
-        cols[j] = S;
+        rest_ones = rest_ones && (__ballot_sync(FULL, !ok) == 0);
     }
-    warp_norm_unsigned(cols, st, d);
+    d0 = __shfl_sync(FULL, d0, 0);
+    const u32 q0 = (u32)ns.col_carry + ns.carry;
+    const u32 T0 = rest_ones ? (d0 >= FULL - 62 ? (u32)(0x100000000ull - d0) : 64u) : 64u;
+    u32 cin = 0;
+    if (lane == 0) {
+        st_rel(st + seg, F_AGG | ((u64)T0 << 32) | q0);
+        u32 q = 0, T = 64;
+        bool have = false;
+        u32 base = 0;
+        for (int j = seg - 1; j >= -1; --j) {
+            u64 v;
+            if (j < 0) v = F_INCL;  // carry into the first segment is 0
+            else v = wait_status(st + j, err);
+            const u32 qj = (u32)(v & 0xffffffffu), Tj = (u32)((v >> 32) & 0x3fffffffu);
+            if ((v & F_MASK) == F_INCL) { base = (j < 0) ? 0u : qj; break; }
+            if (!have) { q = qj; T = Tj; have = true; }
+            else rec_compose(q, T, qj, Tj);  // older map applied first
+        }
+        cin = have ? q + (base >= T ? 1u : 0u) : base;
+        st_rel(st + seg, F_INCL | (u64)(q0 + (cin >= T0 ? 1u : 0u)));
+    }
+    cin = __shfl_sync(FULL, cin, 0);
+    ns.col_carry = cin;
+    ns.carry = 0;
+    const bool aligned = ((reinterpret_cast<uintptr_t>(out) & 15u) == 0);
+    for (int pos = start; pos < end; pos += CH) {
+        u64 cols[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) cols[j] = col(pos + 4 * lane + j);
+        warp_norm_unsigned(cols, ns, d);
+        const int l0 = pos + 4 * lane;
+        if (aligned && l0 + 4 <= out_len) {
+            st4(out + l0, d);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (l0 + j < out_len) out[l0 + j] = d[j];
+        }
+    }
 }
 
 __global__ void __launch_bounds__(128) wide_recompose_kernel(RecArgs a, u64* status, int* counter, int* err) {
     const long total = a.P * (long)a.nseg;
-    const int lane = lane_id();
     for (;;) {
         const long t = next_ticket(counter);
         if (t >= total) return;
         const int seg = (int)(t / a.P);
         const long p = t - (long)seg * a.P;
-        u64* st = status + p * a.nseg;
-        u32* out = a.out + p * a.ostride;
         const int start = seg * WSEG;
         const int end = min(start + WSEG, (a.out_len + CH - 1) / CH * CH);
-        UnsignedNorm ns{0, 0};
-        u32 d[4];
-        u32 d0 = 0;
-        bool rest_ones = true;
-        for (int pos = start; pos < end; pos += CH) {
-            rec_chunk(a, p, pos, ns, d);
-            const int l0 = pos + 4 * lane;
-            bool ok = true;
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int l = l0 + j;
-                if (l == start) d0 = d[j];
-                else if (l < a.out_len && d[j] != FULL) ok = false;
+        auto col = [&](int l) -> u64 {
+            u64 S = 0;
+            if (l < a.out_len) {
+                int tt = l / a.b;
+                if (tt > a.nterms - 1) tt = a.nterms - 1;
+                for (; tt >= 0; --tt) {
+                    const int x = l - tt * a.b;
+                    if (x >= a.Y) break;
+                    S += a.w[tt][p * a.Y + x];
+                }
             }
-            rest_ones = rest_ones && (__ballot_sync(FULL, !ok) == 0);
-        }
-        d0 = __shfl_sync(FULL, d0, 0);
-        const u32 q0 = (u32)ns.col_carry + ns.carry;
-        const u32 T0 = rest_ones ? (d0 >= FULL - 62 ? (u32)(0x100000000ull - d0) : 64u) : 64u;
-        u32 cin = 0;
-        if (lane == 0) {
-            st_rel(st + seg, F_AGG | ((u64)T0 << 32) | q0);
-            u32 q = 0, T = 64;  // identity on carries 0..63 is not of this form: track "none yet"
-            bool have = false;
-            u32 base = 0;
-            for (int j = seg - 1; j >= -1; --j) {
-                u64 v;
-                if (j < 0) v = F_INCL;  // carry into the first segment is 0
-                else v = wait_status(st + j, err);
-                const u32 qj = (u32)(v & 0xffffffffu), Tj = (u32)((v >> 32) & 0x3fffffffu);
-                if ((v & F_MASK) == F_INCL) { base = (j < 0) ? 0u : qj; break; }
-                if (!have) { q = qj; T = Tj; have = true; }
-                else rec_compose(q, T, qj, Tj);  // older map applied first
+            return S;
+        };
+        colnorm_task(col, status + p * a.nseg, seg, start, end, a.out_len, a.out + p * a.ostride, err);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Evaluation of few, huge operand rows: E_j and O_j (even and odd parts at
+// x = 2^j, Section 4 eq. 4.1) normalised segment-parallel, the sign of E - O
+// from the top differing limb, then U(x) = E + O and |U(-x)| by the add/sub
+// pass, and U(0) = u_0 copied.
+// ---------------------------------------------------------------------------
+struct EvalNormArgs {
+    const u32* in;
+    long in_stride;
+    int s, B, b, n, e;
+    u32* EO;      // [2n][P][Ew]: E_j at 2j, O_j at 2j + 1
+    int Ew;
+    long P;
+    int nseg;
+};
+
+__global__ void __launch_bounds__(128) wide_evalnorm_kernel(EvalNormArgs a, u64* status, int* counter, int* err) {
+    const int nch = 2 * a.n;
+    const long total = a.P * nch * (long)a.nseg;
+    for (;;) {
+        const long t = next_ticket(counter);
+        if (t >= total) return;
+        const int seg = (int)(t / (a.P * nch));
+        const long rem = t - (long)seg * a.P * nch;
+        const long p = rem / nch;
+        const int c = (int)(rem - p * nch);
+        const int j = c >> 1, parity = c & 1;
+        const u32* row = a.in + p * a.in_stride;
+        const int start = seg * WSEG;
+        const int end = min(start + WSEG, a.Ew);
+        auto col = [&](int l) -> u64 {
+            u64 S = 0;
+            if (l < a.e) {
+                for (int i = parity; i < a.B; i += 2) {
+                    const int sh = j * i, qa = sh >> 5, r = sh & 31;
+                    const int xh = l - qa, xl = l - qa - 1;
+                    const u32 hi = (xh >= 0 && xh < a.b && i * a.b + xh < a.s) ? __ldg(row + i * a.b + xh) : 0u;
+                    const u32 lo = (xl >= 0 && xl < a.b && i * a.b + xl < a.s) ? __ldg(row + i * a.b + xl) : 0u;
+                    S += fshl(lo, hi, (u32)r);
+                }
             }
-            cin = have ? q + (base >= T ? 1u : 0u) : base;
-            st_rel(st + seg, F_INCL | (u64)(q0 + (cin >= T0 ? 1u : 0u)));
-        }
-        cin = __shfl_sync(FULL, cin, 0);
-        ns.col_carry = cin;
-        ns.carry = 0;
-        const bool aligned = ((reinterpret_cast<uintptr_t>(out) & 15u) == 0);
-        for (int pos = start; pos < end; pos += CH) {
-            rec_chunk(a, p, pos, ns, d);
-            const int l0 = pos + 4 * lane;
-            if (aligned && l0 + 4 <= a.out_len) {
-                st4(out + l0, d);
-            } else {
-#pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    if (l0 + j < a.out_len) out[l0 + j] = d[j];
-            }
-        }
+            return S;
+        };
+        colnorm_task(col, status + (p * nch + c) * a.nseg, seg, start, end, a.Ew,
+                     a.EO + ((long)c * a.P + p) * a.Ew, err);
+    }
+}
+
+// sign of E_j - O_j per (row, j): one block per pair, top differing limb
+__global__ void __launch_bounds__(256) wide_evalsign_kernel(const u32* EO, int Ew, long P, int n,
+                                                            uint8_t* swap, uint8_t* sgn, int npts) {
+    const long pj = blockIdx.x;
+    const long p = pj / n;
+    const int j = (int)(pj - p * n);
+    const u32* E = EO + ((long)(2 * j) * P + p) * Ew;
+    const u32* O = EO + ((long)(2 * j + 1) * P + p) * Ew;
+    __shared__ int best[8];
+    int top = -1;
+    for (int l = threadIdx.x; l < Ew; l += blockDim.x)
+        if (E[l] != O[l]) top = l;
+    for (int o = 16; o; o >>= 1) top = max(top, __shfl_xor_sync(FULL, top, o));
+    if ((threadIdx.x & 31) == 0) best[threadIdx.x >> 5] = top;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = -1;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = max(t, best[w]);
+        const bool neg = t >= 0 && O[t] > E[t];
+        swap[p * n + j] = neg ? 1 : 0;
+        sgn[p * npts + 2 * j + 1] = 0;
+        sgn[p * npts + 2 * j + 2] = neg ? 1 : 0;
+        if (j == 0) sgn[p * npts] = 0;
+    }
+}
+
+// U(0) = u_0 into row 0 of each product's evaluations
+__global__ void wide_evalzero_kernel(const u32* in, long in_stride, int s, int b, u32* out, int estride,
+                                     int npts, long P) {
+    const long total = P * (long)estride;
+    for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < total; q += (long)gridDim.x * blockDim.x) {
+        const long p = q / estride;
+        const int l = (int)(q - p * estride);
+        out[p * npts * (long)estride + l] = (l < b && l < s) ? in[p * in_stride + l] : 0u;
     }
 }
 
@@ -510,6 +611,81 @@ int* wide_error_word(void* work, const LevelGeom& g, long P) {
     return (int*)((char*)work + vals + stat + 2048);
 }
 
+bool use_wide_eval(const LevelGeom& g, long P) { return P * (long)g.n < 152L * 4 && g.e >= 4096; }
+
+static size_t wide_eval_parts(const LevelGeom& g, long P, size_t* stat_off, size_t* swap_off,
+                              size_t* cnt_off) {
+    const int Ew = (g.e + WSEG - 1) / WSEG * WSEG;
+    const long nseg = Ew / WSEG;
+    size_t off = (size_t)2 * g.n * P * Ew * 4;
+    *stat_off = off;
+    off += (size_t)2 * P * 2 * g.n * nseg * 8;
+    *swap_off = off;
+    off += ((size_t)P * g.n + 255) / 256 * 256;
+    *cnt_off = off;
+    return off + 4096;
+}
+
+size_t wide_eval_work_bytes(const LevelGeom& g, long P) {
+    size_t a, b, c;
+    return wide_eval_parts(g, P, &a, &b, &c);
+}
+
+int* wide_eval_error_word(void* work, const LevelGeom& g, long P) {
+    size_t a, b, c;
+    wide_eval_parts(g, P, &a, &b, &c);
+    return (int*)((char*)work + c + 2048);
+}
+
+cudaError_t launch_wide_eval(const u32* in, long in_stride, const LevelGeom& g, u32* out, uint8_t* sgn,
+                             long P, void* work, cudaStream_t st) {
+    size_t stat_off, swap_off, cnt_off;
+    wide_eval_parts(g, P, &stat_off, &swap_off, &cnt_off);
+    char* base = (char*)work;
+    const int Ew = (g.e + WSEG - 1) / WSEG * WSEG;
+    const int nseg = Ew / WSEG;
+    const int n = g.n, npts = 2 * g.B - 1;
+    u32* EO = (u32*)base;
+    u64* stat = (u64*)(base + stat_off);
+    const size_t stat_pass = (size_t)P * 2 * n * nseg;
+    uint8_t* swap = (uint8_t*)(base + swap_off);
+    int* cnt = (int*)(base + cnt_off);
+    int* err = (int*)(base + cnt_off + 2048);
+    cudaError_t e = cudaMemsetAsync(base + stat_off, 0, cnt_off - stat_off + 4096, st);
+    if (e != cudaSuccess) return e;
+    auto grid_for = [&](long tasks) {
+        long b = (tasks + 3) / 4;
+        return (unsigned)(b < 152 * 16 ? (b < 1 ? 1 : b) : 152 * 16);
+    };
+    EvalNormArgs ea;
+    ea.in = in; ea.in_stride = in_stride; ea.s = g.s; ea.B = g.B; ea.b = g.b; ea.n = n; ea.e = g.e;
+    ea.EO = EO; ea.Ew = Ew; ea.P = P; ea.nseg = nseg;
+    wide_evalnorm_kernel<<<grid_for(P * 2 * n * (long)nseg), 128, 0, st>>>(ea, stat, cnt, err);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    wide_evalsign_kernel<<<(unsigned)(P * n), 256, 0, st>>>(EO, Ew, P, n, swap, sgn, npts);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    WidePass wp;
+    wp.nch = 2 * n; wp.nseg = nseg; wp.Y = Ew; wp.P = P;
+    for (int j = 0; j < n; ++j)
+        for (int pm = 0; pm < 2; ++pm) {
+            WideChain& C = wp.ch[2 * j + pm];
+            C.X = EO + (long)(2 * j) * P * Ew; C.sX = Ew; C.lenX = Ew;
+            C.Z = EO + (long)(2 * j + 1) * P * Ew; C.sZ = Ew; C.lenZ = Ew;
+            C.O = out + (long)(2 * j + 1 + pm) * g.estride; C.sO = (long)npts * g.estride;
+            C.lenO = g.estride;
+            C.op = pm;          // U(x) = E + O; |U(-x)| = E - O, operands exchanged when negative
+            C.shift = 0;
+            C.swap = pm ? swap + j : nullptr;
+            C.sSwap = n;
+        }
+    wide_addsub_kernel<<<grid_for(P * 2 * n * (long)nseg), 128, 0, st>>>(wp, stat + stat_pass, cnt + 1, err);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const long tot = P * (long)g.estride;
+    wide_evalzero_kernel<<<(unsigned)std::min<long>((tot + 255) / 256, 152 * 32), 256, 0, st>>>(
+        in, in_stride, g.s, g.b, out, g.estride, npts, P);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_wide_interp(const LevelGeom& g, const u32* y, const uint8_t* su, const uint8_t* sv,
                                u32* out, long out_stride, int out_len, void* work, long P,
                                cudaStream_t st) {
@@ -564,7 +740,7 @@ cudaError_t launch_wide_interp(const LevelGeom& g, const u32* y, const uint8_t* 
                 C.X = y + (long)(2 * m - 1) * g.ystride; C.sX = ys; C.lenX = 2 * g.e;
                 C.Z = y + (long)(2 * m) * g.ystride; C.sZ = ys; C.lenZ = 2 * g.e;
                 C.O = tmp[0] + (long)(2 * (m - 1) + s2) * P * Yw; C.sO = Yw;
-                C.op = s2; C.shift = 0;
+                C.op = s2; C.shift = 0; C.lenO = 0; C.swap = nullptr; C.sSwap = 0;
             }
         // A/D occupy tmp[0 .. 2n) as one [2n][P][Yw] array
         if ((e = run_addsub(wp)) != cudaSuccess) return e;
@@ -589,7 +765,9 @@ cudaError_t launch_wide_interp(const LevelGeom& g, const u32* y, const uint8_t* 
                 S.X = c[m]; S.sX = Yw; S.lenX = Yw;
                 S.Z = c[m - 1]; S.sZ = Yw; S.lenZ = Yw;
                 S.O = tmp[2 * i + poly]; S.sO = Yw; S.op = 1; S.shift = 0;
+                S.lenO = 0; S.swap = nullptr; S.sSwap = 0;
                 WideChain& Dv = wd.ch[2 * i + poly];
+                Dv.lenO = 0; Dv.swap = nullptr; Dv.sSwap = 0;
                 Dv.X = tmp[2 * i + poly]; Dv.sX = Yw; Dv.lenX = Yw;
                 Dv.Z = nullptr; Dv.sZ = 0; Dv.lenZ = 0;
                 Dv.O = c[m]; Dv.sO = Yw;
@@ -613,6 +791,7 @@ cudaError_t launch_wide_interp(const LevelGeom& g, const u32* y, const uint8_t* 
                 S.X = c[kx]; S.sX = Yw; S.lenX = Yw;
                 S.Z = c[kx + 1]; S.sZ = Yw; S.lenZ = Yw;
                 S.O = tmp[2 * i + poly]; S.sO = Yw; S.op = 1; S.shift = 2 * (m - 1);
+                S.lenO = 0; S.swap = nullptr; S.sSwap = 0;
             }
         }
         if ((e = run_addsub(ws)) != cudaSuccess) return e;

@@ -67,3 +67,24 @@ def test_large_all_ones_square(ctx, tc):
     want[L] = 0xFFFFFFFE
     want[L + 1:] = 0xFFFFFFFF
     assert np.array_equal(out, want)
+
+
+@pytest.mark.parametrize("kind", ["equal_halves", "all_ones", "sparse"])
+@pytest.mark.parametrize("plan", [[2, 8, 6, 4], [3, 8, 6, 4], [16, 8, 4]])
+def test_wide_evaluation_sign_edges(ctx, tc, kind, plan):
+    """Top-level evaluation of one long row runs segment-parallel; operands
+    whose even and odd parts cancel (U(-1) = 0), or carry everywhere."""
+    t = tc.tc
+    L = 1 << 16
+    if kind == "equal_halves":
+        h = inputs.uniform(L // 2, 21)
+        a = np.concatenate([h, h])
+        b = np.concatenate([h[::-1], h[::-1]]).copy()
+    elif kind == "all_ones":
+        a = inputs.all_ones(L)
+        b = inputs.all_ones(L)
+    else:
+        a = inputs.sparse(L, 22)
+        b = inputs.sparse(L, 23)
+    out = t.to_numpy(t.tc_mul(ctx, t.to_device(a), t.to_device(b), plan=plan))
+    assert np.array_equal(out, from_int(to_int(a) * to_int(b), 2 * L))
