@@ -3,8 +3,8 @@
 Workload (one "step"): a batch of P balanced products of two 2^20-bit
 operands (32768 uint32 limbs each, limbs uniform from a seed) through the
 whole Toom-Cook path (evaluation, recursive pointwise products, schoolbook
-base case, interpolation, recomposition) in one library call.  P = 608 per
-GPU (4 x 152 SMs), so the operands alone (152 MB) exceed the 129 MB L2 and
+base case, interpolation, recomposition) in one library call.  P = 2432 per
+GPU (16 x 152 SMs), so the operands alone (608 MB) exceed the 129 MB L2 and
 no L2 flush is needed between steps.
 
 Prints one JSON line (rank 0).  `value` is whole-job products per second
@@ -35,10 +35,16 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 LIMBS = 32768            # 2^20 bits
-PER_GPU = 608            # 4 x 152 SMs
+PER_GPU = 2432           # 16 x 152 SMs
 SM_COUNT = 152
 IMAD_PER_CLK_SM = 64     # 32-bit integer multiply(-add) results per clock per SM
 IMAD_PER_LIMB_PRODUCT = 2  # low and high halves of a 32 x 32 -> 64-bit product
+
+# DRAM traffic of the base-case kernel from one ncu capture (profiles/leaf_lane_2e20.md):
+# leaf_lane_kernel<false> on 157320 products of 184 limbs moved 2.651e9 bytes
+# (dram__bytes_read.sum + dram__bytes_write.sum); traffic grows with the number
+# of products, so a launch of N such products moves N * 16851 bytes.
+LEAF_TRAFFIC = {"kernel": "leaf_lane_kernel<false>", "limbs": 184, "bytes_per_product": 2.651e9 / 157320}
 
 
 def parse():
@@ -400,8 +406,14 @@ def main():
         mhz = pk.get("sm_max_mhz", 2070.0)
         peak = SM_COUNT * IMAD_PER_CLK_SM / IMAD_PER_LIMB_PRODUCT * mhz * 1e6 / 1e12
         achieved = top["limb_products"] / top["launches"] / (avg_ms / 1e3) / 1e12
-        roof = {"kernel": "leaf_kernel", "bound": "alu", "achieved": achieved, "peak": peak,
-                "unit": "T limb-products/s", "frac": achieved / peak, "traffic": None,
+        # per launch: bytes = 16 s N and limb products = s^2 N for N products of s limbs
+        leaf_s = int(round(top["limb_products"] / (top["bytes"] / 16.0))) if top["bytes"] else 0
+        n_leaf = top["limb_products"] / top["launches"] / max(1, leaf_s) ** 2 if leaf_s else 0
+        traffic = (n_leaf * LEAF_TRAFFIC["bytes_per_product"]
+                   if leaf_s == LEAF_TRAFFIC["limbs"] else None)
+        roof = {"kernel": "leaf_lane_kernel", "bound": "alu", "achieved": achieved, "peak": peak,
+                "unit": "T limb-products/s", "frac": achieved / peak, "traffic": traffic,
+                "traffic_source": "profiles/leaf_lane_2e20.md (scaled by leaf products)",
                 "peak_source": f"derived: {SM_COUNT} SMs x {IMAD_PER_CLK_SM} IMAD/clk / "
                                f"{IMAD_PER_LIMB_PRODUCT} x {mhz:.0f} MHz"}
     else:
@@ -429,7 +441,7 @@ def main():
             "config": {"workload": f"batch of {P} balanced {L * 32}-bit products per GPU, "
                                    "uniform random limbs (B sweep at 2^20 bits)",
                        "limbs": L, "batch_per_gpu": P, "plan": used_plan,
-                       "l2": "operands (152 MB) exceed the 129 MB L2; no flush"},
+                       "l2": f"operands ({2 * P * L * 4 / 1e6:.0f} MB) exceed the 129 MB L2; no flush"},
             "roofline": roof, "phases": phase_summary, "sweep": sweep,
             "mixed_batch": mixed, "serving": serve,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
