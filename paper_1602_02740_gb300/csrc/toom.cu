@@ -820,6 +820,304 @@ interp_warp_kernel(InterpArgs a, DivTable dt, long P) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Streaming warp-per-product interpolation for values too long for shared
+// memory (many products, long values).
+//
+// Every chain of the even-odd combine and of both Newton loops reads its
+// operands from low limbs to high, carrying a borrow, a division remainder and
+// a few limbs of look-behind, so one warp can push a 32 KL-limb window through
+// all of them before moving on: the values live in shared memory one window
+// at a time and the work buffer is touched a fixed number of times instead of
+// once per chain.
+//
+// Pass A (even-odd combine, Section 4, and Theorem 3.2): a right shift by R
+// needs the limbs above its output, so each right-shifting stage emits the
+// window two limbs lower than its input (offset 2 after the combine, 2kk + 2
+// after stage kk).  Every chain of stage kk reads values written by stage
+// kk - 1, so offsets agree within a stage; c_m is final after stage m, at
+// offset 2(m + 1), and is written to the work buffer at its true position.
+// Pass B (Theorem 3.3) re-reads the final Newton coefficients with aligned
+// windows; its left shifts only look behind.  Pass C recomposes.
+// ---------------------------------------------------------------------------
+
+// e[t] = limb (KL lane - NB + t) of the chunk, t < KL + NB; lane 0 takes the
+// NB limbs below the chunk from h (h[NB - 1] the highest).
+template <int KL, int NB>
+__device__ __forceinline__ void look_behind(const u32 x[KL], const u32 h[NB], u32 e[KL + NB]) {
+    const int lane = lane_id();
+#pragma unroll
+    for (int t = 0; t < NB; ++t) {
+        const u32 v = __shfl_up_sync(FULL, x[KL - NB + t], 1);
+        e[t] = lane == 0 ? h[t] : v;
+    }
+#pragma unroll
+    for (int j = 0; j < KL; ++j) e[NB + j] = x[j];
+}
+
+// Per-warp shared memory: value windows c_1..c_n of both polynomials plus
+// ce_0 (co_0 = 0 is not stored), the even-odd chain states (8 words per
+// node) and the Newton chain states (loop 1: 8 words per chain, both
+// polynomials; loop 2 reuses the space, 6 words per chain).
+struct StreamLayout {
+    int vals, st0, st1, words;
+};
+
+__host__ __device__ inline StreamLayout stream_layout(int n, int C) {
+    StreamLayout L;
+    L.vals = (2 * n + 1) * C;
+    L.st0 = 8 * (n + 1);
+    L.st1 = 4 * n * (n + 1);
+    L.words = L.vals + L.st0 + L.st1;
+    return L;
+}
+
+// Write this lane's KL limbs of a window starting at absolute limb `start`
+// (even) into a row of Y limbs (even), dropping limbs outside [0, Y).
+template <int KL>
+__device__ __forceinline__ void st_window(u32* row, int start, int Y, const u32 v[KL]) {
+    const int p0 = start + KL * lane_id();
+#pragma unroll
+    for (int j = 0; j < KL; j += 2) {
+        const int p = p0 + j;
+        if (p >= 0 && p + 2 <= Y) *reinterpret_cast<uint2*>(row + p) = make_uint2(v[j], v[j + 1]);
+    }
+}
+
+__global__ void __launch_bounds__(256)
+interp_stream_kernel(InterpArgs a, DivTable dt, long P) {
+    constexpr int KL = 4, C = 32 * KL;
+    extern __shared__ __align__(16) u32 sm[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wpb = blockDim.x >> 5;
+    const long k = (long)blockIdx.x * wpb + warp;
+    if (k >= P) return;  // warp-uniform
+    const LevelGeom& g = a.g;
+    const int n = g.n, Y = g.Y, len = 2 * g.e;
+    const int npts = 2 * g.B - 1;
+    const StreamLayout L = stream_layout(n, C);
+    u32* vals = sm + (long)warp * L.words;
+    u32* st0 = vals + L.vals;
+    u32* st1 = st0 + L.st0;
+    u32* W = a.work + k * (long)(2 * (n + 1)) * Y;
+    // this lane's limbs of the window of c_m (m >= 1) or ce_0 (p = 0, m = 0)
+    auto V = [&](int p, int m) -> u32* {
+        return vals + (m == 0 ? 2 * n : p * n + m - 1) * C + KL * lane;
+    };
+    auto Wrow = [&](int p, int m) -> u32* { return W + (long)(p * (n + 1) + m) * Y; };
+    const u32* yk = a.y + k * npts * (long)g.ystride;
+    auto sgn = [&](int p) -> bool {
+        bool s = false;
+        if (a.su) s ^= a.su[k * npts + p] != 0;
+        if (a.sv) s ^= a.sv[k * npts + p] != 0;
+        return s;
+    };
+    auto ldv = [&](const u32* p, u32 v[KL]) {
+        const uint4 q = *reinterpret_cast<const uint4*>(p);
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    };
+    u32 negmask = 0;  // bit m: |W(-2^(m-1))| was negated
+    for (int m = 1; m <= n; ++m) negmask |= sgn(2 * m) ? 1u << m : 0u;
+    for (int i = lane; i < L.st0 + L.st1; i += 32) st0[i] = 0;
+    __syncwarp();
+
+    // ---- pass A: even-odd combine and Newton loop 1 ----
+    const int stepsA = (Y + 2 * n + 2 + C - 1) / C;
+    for (int step = 0; step < stepsA; ++step) {
+        const int base = C * step;  // absolute limb of an offset-0 window
+        __syncwarp();
+        {   // node 0: ce_0 = y_0, co_0 = 0 (delayed by two limbs to offset 2)
+            u32 y0[KL], h[2] = {st0[0], st0[1]}, e[KL + 2], o[KL];
+            ld_seg_masked<KL>(yk, base + KL * lane, len, y0);
+            look_behind<KL, 2>(y0, h, e);
+#pragma unroll
+            for (int j = 0; j < KL; ++j) o[j] = e[j];
+            st_seg<KL>(V(0, 0), o);
+            __syncwarp();
+            if (lane == 31) { st0[0] = y0[KL - 2]; st0[1] = y0[KL - 1]; }
+            st_window<KL>(Wrow(0, 0), base - 2, Y, o);
+        }
+        for (int m = 1; m <= n; ++m) {
+            // eq. 4.5-4.6: A = W(x) + |W(-x)|, D = W(x) - |W(-x)|, x = 2^(m-1);
+            // ce_m = (neg ? D : A) / 2, co_m = x (neg ? A : D) / 2
+            u32* s = st0 + 8 * m;
+            const bool neg = (negmask >> m) & 1u;
+            u32 pv[KL], qv[KL], A[KL], D[KL];
+            ld_seg_masked<KL>(yk + (2 * m - 1) * (long)g.ystride, base + KL * lane, len, pv);
+            ld_seg_masked<KL>(yk + (2 * m) * (long)g.ystride, base + KL * lane, len, qv);
+            u32 cA = s[0], bD = s[1];
+            const u32 hS[3] = {s[2], s[3], s[4]}, hT[3] = {s[5], s[6], s[7]};
+            warp_add_seg<KL>(pv, qv, cA, A);
+            warp_sub_seg<KL>(pv, qv, bD, D);
+            u32 S[KL], T[KL];
+#pragma unroll
+            for (int j = 0; j < KL; ++j) { S[j] = neg ? D[j] : A[j]; T[j] = neg ? A[j] : D[j]; }
+            u32 eS[KL + 3], eT[KL + 3], ce[KL], co[KL];
+            look_behind<KL, 3>(S, hS, eS);
+            look_behind<KL, 3>(T, hT, eT);
+            const u32 sh = m >= 2 ? (u32)(m - 2) : 0u;
+#pragma unroll
+            for (int j = 0; j < KL; ++j) {
+                ce[j] = fshr(eS[j + 1], eS[j + 2], 1);
+                co[j] = m == 1 ? fshr(eT[j + 1], eT[j + 2], 1) : fshl(eT[j], eT[j + 1], sh);
+            }
+            st_seg<KL>(V(0, m), ce);
+            st_seg<KL>(V(1, m), co);
+            __syncwarp();
+            if (lane == 0) { s[0] = cA; s[1] = bD; }
+            if (lane == 31) {
+                s[2] = S[KL - 3]; s[3] = S[KL - 2]; s[4] = S[KL - 1];
+                s[5] = T[KL - 3]; s[6] = T[KL - 2]; s[7] = T[KL - 1];
+            }
+        }
+        // Theorem 3.2, in place with m descending (each update reads the old c_(m-1))
+        int t1 = 0;  // index of chain (kk, kk)
+        for (int kk = 1; kk <= n; ++kk) {
+            for (int m = n; m >= kk; --m) {
+                const int R = m == kk ? 2 * (m - 1) : 2 * (m - kk - 1);
+                const int q = R >> 5;
+                const u32 r = (u32)(R & 31);
+                const bool div = m > kk;
+                const DivConst& d1 = dt.d[0][div ? kk : 0];
+                const DivConst& d2 = dt.d[1][div ? kk : 0];
+                // per polynomial: 2 limbs of look-behind, first remainder | borrow << 31
+                // (remainders are below d < 2^31), second remainder
+                u32* s = st1 + 8 * (t1 + m - kk);
+                u32 out[2][KL], dtop[2][2], bw[2] = {s[2] >> 31, s[6] >> 31};
+#pragma unroll
+                for (int p = 0; p < 2; ++p) {
+                    u32 x[KL], z[KL] = {0, 0, 0, 0}, dv[KL], e[KL + 2];
+                    ldv(V(p, m), x);
+                    if (m > 1 || p == 0) ldv(V(p, m - 1), z);
+                    const u32 h[2] = {s[4 * p], s[4 * p + 1]};
+                    warp_sub_seg<KL>(x, z, bw[p], dv);
+                    look_behind<KL, 2>(dv, h, e);
+#pragma unroll
+                    for (int j = 0; j < KL; ++j)
+                        out[p][j] = q ? fshr(e[j + 1], e[j + 2], r) : fshr(e[j], e[j + 1], r);
+                    dtop[p][0] = dv[KL - 2];
+                    dtop[p][1] = dv[KL - 1];
+                }
+                u32 B1[2] = {s[2] & 0x7fffffffu, s[6] & 0x7fffffffu}, B2[2] = {s[3], s[7]};
+                if (d1.d > 1) {
+#pragma unroll
+                    for (int p = 0; p < 2; ++p) warp_exact_div_seg<KL>(out[p], d1, B1[p]);
+                }
+                if (d2.d > 1) {
+#pragma unroll
+                    for (int p = 0; p < 2; ++p) warp_exact_div_seg<KL>(out[p], d2, B2[p]);
+                }
+#pragma unroll
+                for (int p = 0; p < 2; ++p) st_seg<KL>(V(p, m), out[p]);
+                __syncwarp();
+                if (lane == 0) {
+                    s[2] = B1[0] | bw[0] << 31; s[3] = B2[0];
+                    s[6] = B1[1] | bw[1] << 31; s[7] = B2[1];
+                }
+                if (lane == 31) {
+                    s[0] = dtop[0][0]; s[1] = dtop[0][1];
+                    s[4] = dtop[1][0]; s[5] = dtop[1][1];
+                }
+            }
+            t1 += n - kk + 1;
+            // c_kk is final, at offset 2 kk + 2
+            u32 v[KL];
+            ldv(V(0, kk), v);
+            st_window<KL>(Wrow(0, kk), base - 2 * kk - 2, Y, v);
+            ldv(V(1, kk), v);
+            st_window<KL>(Wrow(1, kk), base - 2 * kk - 2, Y, v);
+        }
+    }
+    __syncwarp();
+    for (int i = lane; i < L.st1; i += 32) st1[i] = 0;
+    __syncwarp();
+
+    // ---- pass B: Newton to monomial basis (Theorem 3.3), aligned windows ----
+    for (int base = 0; base < Y; base += C) {
+        __syncwarp();
+        for (int p = 0; p < 2; ++p)
+            for (int m = 1; m <= n; ++m) {
+                u32 v[KL];
+                ld_seg<KL>(Wrow(p, m) + base + KL * lane, v);
+                st_seg<KL>(V(p, m), v);
+            }
+        // in place with kx ascending (each update reads the old c_(kx+1))
+        int t2 = 0;  // index of chain (m, m)
+        for (int m = n - 1; m >= 1; --m) {
+            const int S = 2 * (m - 1);
+            const int q = S >> 5;
+            const u32 sh = (u32)(S & 31);
+            for (int kx = m; kx <= n - 1; ++kx) {
+                u32* s = st1 + 6 * (t2 + kx - m);
+                u32 ztop[2][2];
+#pragma unroll
+                for (int p = 0; p < 2; ++p) {
+                    u32 x[KL], z[KL], e[KL + 2], sz[KL], r[KL];
+                    ldv(V(p, kx), x);
+                    ldv(V(p, kx + 1), z);
+                    u32 bw = s[3 * p];
+                    const u32 h[2] = {s[3 * p + 1], s[3 * p + 2]};
+                    look_behind<KL, 2>(z, h, e);
+#pragma unroll
+                    for (int j = 0; j < KL; ++j)
+                        sz[j] = q ? fshl(e[j], e[j + 1], sh) : fshl(e[j + 1], e[j + 2], sh);
+                    warp_sub_seg<KL>(x, sz, bw, r);
+                    st_seg<KL>(V(p, kx), r);
+                    ztop[p][0] = z[KL - 2];
+                    ztop[p][1] = z[KL - 1];
+                    __syncwarp();
+                    if (lane == 0) s[3 * p] = bw;
+                    if (lane == 31) { s[3 * p + 1] = ztop[p][0]; s[3 * p + 2] = ztop[p][1]; }
+                }
+            }
+            t2 += n - m;
+        }
+        for (int p = 0; p < 2; ++p)
+            for (int m = 1; m <= n - 1; ++m) {
+                u32 v[KL];
+                ldv(V(p, m), v);
+                st_seg<KL>(Wrow(p, m) + base + KL * lane, v);
+            }
+    }
+    __syncwarp();
+
+    // ---- pass C: recompose out[l] = sum_t w_t[l - t b], w_2i = ce_i, w_2i+1 = co_(i+1) ----
+    u32* out = a.out + k * a.out_stride;
+    const bool aligned = ((reinterpret_cast<uintptr_t>(out) & 15u) == 0);
+    UnsignedNorm nst{0, 0};
+    const int nterms = 2 * n + 1;
+    for (int base_l = 0; base_l < a.out_len; base_l += CH) {
+        u64 cols[4];
+        const int l0 = base_l + 4 * lane;
+        const int t0 = l0 / g.b;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int l = l0 + j;
+            u64 S = 0;
+            if (l < a.out_len) {
+                int t = t0;
+                while ((t + 1) * g.b <= l) ++t;  // t = floor(l / b)
+                if (t > nterms - 1) t = nterms - 1;
+                for (; t >= 0; --t) {
+                    const int x = l - t * g.b;
+                    if (x >= Y) break;
+                    S += Wrow(t & 1, (t + 1) >> 1)[x];
+                }
+            }
+            cols[j] = S;
+        }
+        u32 d[4];
+        warp_norm_unsigned(cols, nst, d);
+        if (aligned && l0 + 4 <= a.out_len) {
+            st4(out + l0, d);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (l0 + j < a.out_len) out[l0 + j] = d[j];
+        }
+    }
+}
+
 // Kernel choice for a level: many products -> one warp per product (values in
 // shared memory when they fit, else in the work buffer); few products -> one
 // block per product.
@@ -827,6 +1125,8 @@ static bool use_warp_kernel(const LevelGeom& g, long P) { return P >= 2048; }
 static size_t warp_values_bytes(const LevelGeom& g) { return (size_t)2 * (g.n + 1) * g.Y * 4; }
 static size_t block_values_bytes(const LevelGeom& g) { return (size_t)4 * (g.n + 1) * g.Y * 4; }
 constexpr size_t WARP_SMEM_MAX = 24 * 1024;
+constexpr int STREAM_SMEM_MAX = 227 * 1024;  // per block
+constexpr int SM_SMEM_BYTES = 228 * 1024;    // per SM
 constexpr size_t BLOCK_SMEM_MAX = 160 * 1024;
 
 size_t interp_work_bytes(const LevelGeom& g, long P) {
@@ -852,6 +1152,29 @@ cudaError_t launch_interp(const LevelGeom& g, const u32* y, const uint8_t* su, c
         a.g = g; a.y = y; a.su = su; a.sv = sv; a.out = out; a.out_stride = out_stride;
         a.out_len = out_len; a.work = work; a.use_smem = warp_smem <= WARP_SMEM_MAX;
         if (!a.use_smem && !work) return cudaErrorInvalidValue;
+        if (!a.use_smem) {
+            // long values: stream windows through shared memory; pick the warps per
+            // block that keep the most warps resident (1 KB reserved per block)
+            const int per_warp = stream_layout(g.n, 128).words * 4;
+            int best_w = 1, best_res = 0;
+            for (int w = 1; w <= 8; ++w) {
+                if (w * per_warp > STREAM_SMEM_MAX) break;
+                int blocks = SM_SMEM_BYTES / (w * per_warp + 1024);
+                if (blocks > 32) blocks = 32;
+                int res = blocks * w;
+                if (res > 64) res = 64;
+                if (res >= best_res) { best_res = res; best_w = w; }
+            }
+            if (best_res == 0) return cudaErrorInvalidConfiguration;
+            static std::once_flag stream_once;
+            std::call_once(stream_once, [] {
+                cudaFuncSetAttribute(interp_stream_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     STREAM_SMEM_MAX);
+            });
+            const long grid = (P + best_w - 1) / best_w;
+            interp_stream_kernel<<<(unsigned)grid, best_w * 32, (size_t)best_w * per_warp, st>>>(a, dt, P);
+            return cudaGetLastError();
+        }
         int wpb = a.use_smem ? (int)((96 * 1024) / warp_smem) : 4;
         if (wpb > 8) wpb = 8;
         if (wpb < 1) wpb = 1;

@@ -258,7 +258,10 @@ def test_square_lane_kernel(tc, L):
 # ---------------------------------------------------------------- many small interpolations
 # 2048 or more products with small values select the warp-per-product kernel.
 
-@pytest.mark.parametrize("B,L", [(2, 9), (3, 100), (4, 259), (8, 130), (3, 2), (4, 2000), (8, 2055)])
+# values over 24 KB per product ((4, 2000) onward) take the streaming kernel; (20, 4000) has
+# right shifts of 32 bits or more, (32, 3000) two divisors per Newton step
+@pytest.mark.parametrize("B,L", [(2, 9), (3, 100), (4, 259), (8, 130), (3, 2), (4, 2000), (8, 2055),
+                                 (12, 6000), (20, 4000), (32, 3000)])
 def test_interpolate_many_products(tc, B, L):
     import torch
     count = 2100
@@ -279,6 +282,23 @@ def test_interpolate_many_products(tc, B, L):
     out = host(tc.tc.tc_toom_interpolate(dev(Y), L, B, SGN_U=torch.from_numpy(S).cuda()))
     for k in check:
         assert same_limbs(out[k], to_int(A[k]) * to_int(Bm[k])), (B, L, k)
+
+
+def test_uniform_batch_bench_launch(ctx, tc):
+    """The timed workload in its own launch configuration: 2432 products of
+    2^20-bit operands in one call, plan [12, 5, 3] (levels of 2432, 55 936 and
+    503 424 products; 2 522 880 base-case products of 184 limbs).  Every
+    product is checked modulo three 61-bit primes, sampled ones exactly."""
+    L, count = 32768, 2432
+    A = np.stack([inputs.uniform(L, 1000 + 2 * k) for k in range(count)])
+    B = np.stack([inputs.uniform(L, 1001 + 2 * k) for k in range(count)])
+    A[5] = 0xFFFFFFFF
+    B[5] = 0xFFFFFFFF
+    OUT = host(tc.tc.tc_mul_uniform(ctx, dev(A), dev(B), plan=[12, 5, 3]))
+    for k in (0, 5, 1217, count - 1):
+        assert same_limbs(OUT[k], to_int(A[k]) * to_int(B[k])), k
+    for k in range(count):
+        assert residues.product_residues_match(A[k], B[k], OUT[k]), k
 
 
 @pytest.mark.parametrize("plan", [[16, 8, 3], [16, 4, 4], [8, 8, 4], [32, 8]])
