@@ -461,10 +461,174 @@ leaf_lane_smem_kernel(const u32* __restrict__ A, long lda, const u32* __restrict
     }
 }
 
+// ---------------------------------------------------------------------------
+// Pair-per-product schoolbook for large batches, operands staged in shared
+// memory.
+//
+// A warp takes 16 products; lanes 2q and 2q+1 share product q.  Both walk the
+// same 8x8 tiles (I, J) by anti-diagonal D = I + J, lane 2q+h multiplying
+// rows 8I+4h .. 8I+4h+3 of a by the eight limbs 8J .. 8J+7 of b, so its
+// products land in columns 8D+4h .. 8D+4h+10: twelve 96-bit Comba
+// accumulators, slot k holding column 8D+4h+k.  After diagonal D the odd lane
+// hands its slots 0..7 (columns 8D+4 .. 8D+11, which it will not touch again)
+// to the even lane, which then holds columns 8D .. 8D+7 complete and emits
+// them through a 64-bit running carry; both lanes slide their windows by
+// eight columns.  A final diagonal with no tiles flushes the top columns.
+//
+// Every operand limb is read from global memory once (coalesced, into
+// shared memory).  Rows are staged with a stride of 8 (mod 32) words, so the
+// 16-byte slice loads of the lane pairs of four products (a quarter warp)
+// fall in distinct bank groups, and both lanes of a pair read the same b
+// slice (a broadcast).
+//
+// Squaring accumulates a_i a_j for i < j only (tiles I <= J; inside a
+// diagonal tile the even/odd rows keep columns c > row) and doubles at
+// emission, adding a_i^2 on the even columns.
+// ---------------------------------------------------------------------------
+constexpr int PAIR_WARPS = 2;
+
+__host__ __device__ inline int pair_stride(int s) {
+    const int sp = (s + 7) / 8 * 8;
+    return sp + (40 - sp % 32) % 32;  // smallest >= sp that is 8 (mod 32)
+}
+
+__device__ __forceinline__ void add96(u32& lo, u32& mid, u32& hi, u32 a, u32 b, u32 c) {
+    asm("add.cc.u32 %0, %0, %3;\n\t"
+        "addc.cc.u32 %1, %1, %4;\n\t"
+        "addc.u32 %2, %2, %5;"
+        : "+r"(lo), "+r"(mid), "+r"(hi)
+        : "r"(a), "r"(b), "r"(c));
+}
+
+template <bool SQ>
+__global__ void __launch_bounds__(32 * PAIR_WARPS)
+leaf_pair_kernel(const u32* __restrict__ A, long lda, const u32* __restrict__ Bm, long ldb,
+                 u32* __restrict__ OUT, long ldo, int s, long P, int vec) {
+    extern __shared__ __align__(16) u32 psm[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int T = (s + 7) / 8, sp = pair_stride(s);
+    u32* sa = psm + (long)warp * (SQ ? 1 : 2) * 16 * sp;
+    u32* sb = SQ ? sa : sa + 16 * sp;
+    const long pw = ((long)blockIdx.x * PAIR_WARPS + warp) * 16;  // first product of the warp
+    for (int q = 0; q < 16; ++q) {
+        const long pq = pw + q;
+        const bool ok = pq < P;
+        const u32* ra = A + (ok ? pq : 0) * lda;
+        const u32* rb = Bm + (ok ? pq : 0) * ldb;
+        for (int i = 4 * lane; i < 8 * T; i += 128) {
+            u32 va[4], vb[4];
+            if (ok && vec && i + 4 <= s) {
+                const uint4 x = ld4(ra + i);
+                va[0] = x.x; va[1] = x.y; va[2] = x.z; va[3] = x.w;
+                if (!SQ) {
+                    const uint4 y = ld4(rb + i);
+                    vb[0] = y.x; vb[1] = y.y; vb[2] = y.z; vb[3] = y.w;
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    va[j] = ok && i + j < s ? ra[i + j] : 0u;
+                    if (!SQ) vb[j] = ok && i + j < s ? rb[i + j] : 0u;
+                }
+            }
+            st4(sa + q * sp + i, va);
+            if (!SQ) st4(sb + q * sp + i, vb);
+        }
+    }
+    __syncwarp();
+
+    const int q = lane >> 1, h = lane & 1;
+    const long p = pw + q;
+    const bool emit = p < P && h == 0;
+    const u32* ra = sa + q * sp;
+    const u32* rb = sb + q * sp;
+    u32* out = OUT + (p < P ? p : 0) * ldo;
+    const bool aligned = ((reinterpret_cast<uintptr_t>(out) & 15u) == 0);
+    const int out_len = 2 * s;
+    u32 lo[12], mid[12], hi[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) { lo[k] = 0; mid[k] = 0; hi[k] = 0; }
+    u64 carry = 0;
+    for (int D = 0; D <= 2 * T - 1; ++D) {
+        const int Ilo = D - T + 1 > 0 ? D - T + 1 : 0;
+        int Ihi = D < T - 1 ? D : T - 1;
+        if (SQ && Ihi > D / 2) Ihi = D / 2;
+        for (int I = Ilo; I <= Ihi; ++I) {
+            const int J = D - I;
+            const uint4 av = ld4(ra + 8 * I + 4 * h);
+            const uint4 b0 = ld4(rb + 8 * J), b1 = ld4(rb + 8 * J + 4);
+            const u32 a4[4] = {av.x, av.y, av.z, av.w};
+            const u32 b8[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+            if (SQ && I == J) {
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int c = 0; c < 8; ++c)
+                        mac96(lo[r + c], mid[r + c], hi[r + c], a4[r], c > 4 * h + r ? b8[c] : 0u);
+            } else {
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) mac96(lo[r + c], mid[r + c], hi[r + c], a4[r], b8[c]);
+            }
+        }
+        // the odd lane's slots 0..7 join the even lane's slots 4..11
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const u32 pl = __shfl_down_sync(FULL, lo[k], 1);
+            const u32 pm = __shfl_down_sync(FULL, mid[k], 1);
+            const u32 ph = __shfl_down_sync(FULL, hi[k], 1);
+            if (h == 0) add96(lo[k + 4], mid[k + 4], hi[k + 4], pl, pm, ph);
+        }
+        if (h == 0) {
+            u32 res[8];
+            uint4 sq = make_uint4(0, 0, 0, 0);
+            if (SQ) sq = ld4(ra + 4 * D);  // a_(4D + k/2) for the even columns (zeros past s)
+            const u32 sq4[4] = {sq.x, sq.y, sq.z, sq.w};
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                u64 vlo = lo[k], vmid = mid[k], vhi = hi[k];
+                if (SQ) {
+                    vhi = (vhi << 1) | (vmid >> 31);
+                    vmid = ((vmid << 1) & 0xffffffffull) | (vlo >> 31);
+                    vlo = (vlo << 1) & 0xffffffffull;
+                    if ((k & 1) == 0) {
+                        const u64 x = (u64)sq4[k / 2] * sq4[k / 2];
+                        vlo += x & 0xffffffffull;
+                        vmid += x >> 32;
+                    }
+                }
+                const u64 t = vlo + (carry & 0xffffffffull);
+                res[k] = (u32)t;
+                carry = (carry >> 32) + (t >> 32) + vmid + (vhi << 32);
+            }
+            if (emit) {
+                const int c0 = 8 * D;
+                if (aligned && c0 + 8 <= out_len) {
+                    st4(out + c0, res);
+                    st4(out + c0 + 4, res + 4);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 8; ++k)
+                        if (c0 + k < out_len) out[c0 + k] = res[k];
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            lo[k] = k + 8 < 12 ? lo[k + 8] : 0u;
+            mid[k] = k + 8 < 12 ? mid[k + 8] : 0u;
+            hi[k] = k + 8 < 12 ? hi[k + 8] : 0u;
+        }
+    }
+}
+
 // Products at or above this count use the lane-per-product kernels.
 constexpr long LANE_KERNEL_MIN = 4096;
-// Operands at or below this length are staged in shared memory.
+// Operands at or below this length are staged in shared memory one product per
+// lane; longer ones two lanes per product while the block's rows fit.
 constexpr int LANE_SMEM_MAX = 136;
+constexpr size_t PAIR_SMEM_MAX = 200 * 1024;
 
 cudaError_t launch_leaf(const u32* A, long lda, const u32* Bm, long ldb, u32* OUT, long ldo,
                         int s, long P, cudaStream_t st) {
@@ -490,6 +654,21 @@ cudaError_t launch_leaf(const u32* A, long lda, const u32* Bm, long ldb, u32* OU
     if (P >= LANE_KERNEL_MIN) {
         const bool vec = ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(Bm)) & 15u) == 0 &&
                          lda % 4 == 0 && ldb % 4 == 0;
+        const size_t per_warp = (size_t)(square ? 1 : 2) * 16 * pair_stride(s) * 4;
+        if (per_warp * PAIR_WARPS <= PAIR_SMEM_MAX) {
+            static std::once_flag pair_once;
+            std::call_once(pair_once, [] {
+                cudaFuncSetAttribute(leaf_pair_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, PAIR_SMEM_MAX);
+                cudaFuncSetAttribute(leaf_pair_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, PAIR_SMEM_MAX);
+            });
+            const unsigned grid = (unsigned)((P + 16 * PAIR_WARPS - 1) / (16 * PAIR_WARPS));
+            const size_t smem = per_warp * PAIR_WARPS;
+            if (square)
+                leaf_pair_kernel<true><<<grid, 32 * PAIR_WARPS, smem, st>>>(A, lda, Bm, ldb, OUT, ldo, s, P, vec);
+            else
+                leaf_pair_kernel<false><<<grid, 32 * PAIR_WARPS, smem, st>>>(A, lda, Bm, ldb, OUT, ldo, s, P, vec);
+            return cudaGetLastError();
+        }
         const unsigned grid = (unsigned)((P + 127) / 128);
         if (square)
             leaf_lane_kernel<true><<<grid, 128, 0, st>>>(A, lda, Bm, ldb, OUT, ldo, s, P, vec);

@@ -221,9 +221,12 @@ def test_batch_mixed_sizes(ctx, tc):
 
 
 # ---------------------------------------------------------------- base case, large batches
-# 4096 or more products select the lane-per-product kernel.
+# 4096 or more products select the lane-per-product kernels: one lane per
+# product up to 136 limbs, a lane pair per product (rows in shared memory)
+# up to 792 limbs, one lane per product from global memory beyond.
 
-@pytest.mark.parametrize("L", [1, 3, 7, 8, 9, 31, 63, 64, 65, 88, 100, 128, 137, 200])
+@pytest.mark.parametrize("L", [1, 3, 7, 8, 9, 31, 63, 64, 65, 88, 100, 128, 137, 184, 200, 224,
+                               300, 511, 800])
 @pytest.mark.parametrize("layout", ["aligned", "strided"])
 def test_schoolbook_lane_kernel(tc, L, layout):
     count = 4100
@@ -243,7 +246,7 @@ def test_schoolbook_lane_kernel(tc, L, layout):
         assert np.array_equal(out[k], native.schoolbook(A[k], B[k])), (L, k)
 
 
-@pytest.mark.parametrize("L", [1, 2, 8, 9, 15, 16, 17, 64, 88, 130])
+@pytest.mark.parametrize("L", [1, 2, 8, 9, 15, 16, 17, 64, 88, 130, 137, 184, 255, 800])
 def test_square_lane_kernel(tc, L):
     count = 4200
     g = inputs.rng(1000 + L)
