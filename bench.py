@@ -40,11 +40,11 @@ SM_COUNT = 152
 IMAD_PER_CLK_SM = 64     # 32-bit integer multiply(-add) results per clock per SM
 IMAD_PER_LIMB_PRODUCT = 2  # low and high halves of a 32 x 32 -> 64-bit product
 
-# DRAM traffic of the base-case kernel from one ncu capture (profiles/leaf_lane_2e20.md):
-# leaf_lane_kernel<false> on 157320 products of 184 limbs moved 2.651e9 bytes
+# DRAM traffic of the base-case kernel from one ncu capture (profiles/leaf_pair_2e20.md):
+# leaf_pair_kernel<false> on 157320 products of 184 limbs moved 4.142e8 bytes
 # (dram__bytes_read.sum + dram__bytes_write.sum); traffic grows with the number
-# of products, so a launch of N such products moves N * 16851 bytes.
-LEAF_TRAFFIC = {"kernel": "leaf_lane_kernel<false>", "limbs": 184, "bytes_per_product": 2.651e9 / 157320}
+# of products, so a launch of N such products moves N * 2633 bytes.
+LEAF_TRAFFIC = {"kernel": "leaf_pair_kernel<false>", "limbs": 184, "bytes_per_product": 4.142e8 / 157320}
 
 
 def parse():
@@ -409,11 +409,15 @@ def main():
         # per launch: bytes = 16 s N and limb products = s^2 N for N products of s limbs
         leaf_s = int(round(top["limb_products"] / (top["bytes"] / 16.0))) if top["bytes"] else 0
         n_leaf = top["limb_products"] / top["launches"] / max(1, leaf_s) ** 2 if leaf_s else 0
+        # the library's base-case choice: tile kernel below 4096 products, else one
+        # lane per product up to 136 limbs, a lane pair per product above
+        kname = ("leaf_kernel" if n_leaf < 4096 else
+                 "leaf_lane_smem_kernel<false>" if leaf_s <= 136 else "leaf_pair_kernel<false>")
         traffic = (n_leaf * LEAF_TRAFFIC["bytes_per_product"]
-                   if leaf_s == LEAF_TRAFFIC["limbs"] else None)
-        roof = {"kernel": "leaf_lane_kernel", "bound": "alu", "achieved": achieved, "peak": peak,
+                   if leaf_s == LEAF_TRAFFIC["limbs"] and kname == LEAF_TRAFFIC["kernel"] else None)
+        roof = {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": peak,
                 "unit": "T limb-products/s", "frac": achieved / peak, "traffic": traffic,
-                "traffic_source": "profiles/leaf_lane_2e20.md (scaled by leaf products)",
+                "traffic_source": "profiles/leaf_pair_2e20.md (scaled by leaf products)",
                 "peak_source": f"derived: {SM_COUNT} SMs x {IMAD_PER_CLK_SM} IMAD/clk / "
                                f"{IMAD_PER_LIMB_PRODUCT} x {mhz:.0f} MHz"}
     else:
