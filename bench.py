@@ -409,10 +409,12 @@ def main():
         # per launch: bytes = 16 s N and limb products = s^2 N for N products of s limbs
         leaf_s = int(round(top["limb_products"] / (top["bytes"] / 16.0))) if top["bytes"] else 0
         n_leaf = top["limb_products"] / top["launches"] / max(1, leaf_s) ** 2 if leaf_s else 0
-        # the library's base-case choice: tile kernel below 4096 products, else one
-        # lane per product up to 136 limbs, a lane pair per product above
+        # the library's base-case choice: tile kernel below 4096 products, else a
+        # lane pair per product while a block's rows (256 x stride bytes) fit 200 KB
+        sp = -(-leaf_s // 8) * 8
+        sp += 8 if sp % 32 in (0, 16) else 0
         kname = ("leaf_kernel" if n_leaf < 4096 else
-                 "leaf_lane_smem_kernel<false>" if leaf_s <= 136 else "leaf_pair_kernel<false>")
+                 "leaf_pair_kernel<false>" if 256 * sp <= 200 * 1024 else "leaf_lane_kernel<false>")
         traffic = (n_leaf * LEAF_TRAFFIC["bytes_per_product"]
                    if leaf_s == LEAF_TRAFFIC["limbs"] and kname == LEAF_TRAFFIC["kernel"] else None)
         roof = {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": peak,

@@ -368,99 +368,6 @@ cudaError_t launch_schoolbook_big(const u32* A, long lda, const u32* Bm, long ld
     return cudaGetLastError();
 }
 
-// The same schedule with the warp's 32 products staged in shared memory first
-// (coalesced row reads, stored transposed as [limb][33] so both the staging
-// writes and the per-lane slice reads are free of bank conflicts): every
-// operand limb is read from global memory once.
-template <bool SQ>
-__global__ void __launch_bounds__(64)
-leaf_lane_smem_kernel(const u32* __restrict__ A, long lda, const u32* __restrict__ Bm, long ldb,
-                      u32* __restrict__ OUT, long ldo, int s, long P) {
-    extern __shared__ u32 lsm[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int T = (s + 7) / 8;
-    const int sp = 8 * T;  // staged limbs per operand (zeros beyond s)
-    u32* sa = lsm + (long)warp * (SQ ? 1 : 2) * sp * 33;
-    u32* sb = SQ ? sa : sa + sp * 33;
-    const long pw = ((long)blockIdx.x * (blockDim.x >> 5) + warp) * 32;  // first product of the warp
-    // stage: product q's limb i at [i][q]
-    for (int q = 0; q < 32; ++q) {
-        const long pq = pw + q < P ? pw + q : P - 1;
-        const u32* ra = A + pq * lda;
-        const u32* rb = Bm + pq * ldb;
-        for (int i = lane; i < sp; i += 32) {
-            sa[i * 33 + q] = i < s ? ra[i] : 0u;
-            if (!SQ) sb[i * 33 + q] = i < s ? rb[i] : 0u;
-        }
-    }
-    __syncwarp();
-    const long p0 = pw + lane;
-    const bool active = p0 < P;
-    u32* out = OUT + (active ? p0 : 0) * ldo;
-    const int out_len = 2 * s;
-    u32 lo[15], mid[15], hi[15];
-#pragma unroll
-    for (int k = 0; k < 15; ++k) { lo[k] = 0; mid[k] = 0; hi[k] = 0; }
-    u64 carry = 0;
-    for (int D = 0; D <= 2 * T - 2; ++D) {
-        const int Ilo = D - T + 1 > 0 ? D - T + 1 : 0;
-        const int Ihi = D < T - 1 ? D : T - 1;
-        for (int I = Ilo; I <= Ihi; ++I) {
-            const int J = D - I;
-            if (SQ && I > J) break;
-            u32 a8[8], b8[8];
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                a8[k] = sa[(8 * I + k) * 33 + lane];
-                b8[k] = sb[(8 * J + k) * 33 + lane];
-            }
-            if (SQ && I == J) {
-#pragma unroll
-                for (int r = 0; r < 8; ++r)
-#pragma unroll
-                    for (int c = r + 1; c < 8; ++c) mac96(lo[r + c], mid[r + c], hi[r + c], a8[r], b8[c]);
-            } else {
-#pragma unroll
-                for (int r = 0; r < 8; ++r)
-#pragma unroll
-                    for (int c = 0; c < 8; ++c) mac96(lo[r + c], mid[r + c], hi[r + c], a8[r], b8[c]);
-            }
-        }
-        const bool last = D == 2 * T - 2;
-#pragma unroll
-        for (int k = 0; k < 15; ++k) {
-            if (k >= 8 && !last) break;
-            u64 vlo = lo[k], vmid = mid[k], vhi = hi[k];
-            if (SQ) {
-                vhi = (vhi << 1) | (vmid >> 31);
-                vmid = ((vmid << 1) & 0xffffffffull) | (vlo >> 31);
-                vlo = (vlo << 1) & 0xffffffffull;
-                if ((k & 1) == 0) {
-                    const int i = 4 * D + k / 2;
-                    const u32 x = i < sp ? sa[i * 33 + lane] : 0u;
-                    const u64 sqv = (u64)x * x;
-                    vlo += sqv & 0xffffffffull;
-                    vmid += sqv >> 32;
-                }
-            }
-            const u64 t = vlo + (carry & 0xffffffffull);
-            const int c = 8 * D + k;
-            if (active && c < out_len) out[c] = (u32)t;
-            carry = (carry >> 32) + (t >> 32) + vmid + (vhi << 32);
-        }
-        if (last) {
-            const int c = 8 * D + 15;
-            if (active && c < out_len) out[c] = (u32)carry;
-        }
-#pragma unroll
-        for (int k = 0; k < 15; ++k) {
-            lo[k] = k + 8 < 15 ? lo[k + 8] : 0u;
-            mid[k] = k + 8 < 15 ? mid[k + 8] : 0u;
-            hi[k] = k + 8 < 15 ? hi[k + 8] : 0u;
-        }
-    }
-}
-
 // ---------------------------------------------------------------------------
 // Pair-per-product schoolbook for large batches, operands staged in shared
 // memory.
@@ -476,10 +383,10 @@ leaf_lane_smem_kernel(const u32* __restrict__ A, long lda, const u32* __restrict
 // eight columns.  A final diagonal with no tiles flushes the top columns.
 //
 // Every operand limb is read from global memory once (coalesced, into
-// shared memory).  Rows are staged with a stride of 8 (mod 32) words, so the
-// 16-byte slice loads of the lane pairs of four products (a quarter warp)
-// fall in distinct bank groups, and both lanes of a pair read the same b
-// slice (a broadcast).
+// shared memory).  Rows are staged with a stride of 8 or 24 (mod 32) words,
+// so the 16-byte slice loads of the lane pairs of four products (a quarter
+// warp) fall in distinct bank groups, and both lanes of a pair read the same
+// b slice (a broadcast).
 //
 // Squaring accumulates a_i a_j for i < j only (tiles I <= J; inside a
 // diagonal tile the even/odd rows keep columns c > row) and doubles at
@@ -488,8 +395,9 @@ leaf_lane_smem_kernel(const u32* __restrict__ A, long lda, const u32* __restrict
 constexpr int PAIR_WARPS = 2;
 
 __host__ __device__ inline int pair_stride(int s) {
-    const int sp = (s + 7) / 8 * 8;
-    return sp + (40 - sp % 32) % 32;  // smallest >= sp that is 8 (mod 32)
+    int sp = (s + 7) / 8 * 8;  // a multiple of 8 words: 8 or 24 (mod 32) wanted
+    if (sp % 32 == 0 || sp % 32 == 16) sp += 8;
+    return sp;
 }
 
 __device__ __forceinline__ void add96(u32& lo, u32& mid, u32& hi, u32 a, u32 b, u32 c) {
@@ -623,34 +531,16 @@ leaf_pair_kernel(const u32* __restrict__ A, long lda, const u32* __restrict__ Bm
     }
 }
 
-// Products at or above this count use the lane-per-product kernels.
+// Products at or above this count use the lane-per-product kernels: a lane
+// pair per product with the rows in shared memory while a block's rows fit,
+// else one lane per product reading its rows from global memory.
 constexpr long LANE_KERNEL_MIN = 4096;
-// Operands at or below this length are staged in shared memory one product per
-// lane; longer ones two lanes per product while the block's rows fit.
-constexpr int LANE_SMEM_MAX = 136;
 constexpr size_t PAIR_SMEM_MAX = 200 * 1024;
 
 cudaError_t launch_leaf(const u32* A, long lda, const u32* Bm, long ldb, u32* OUT, long ldo,
                         int s, long P, cudaStream_t st) {
     if (P <= 0) return cudaSuccess;
     const bool square = (A == Bm && lda == ldb);
-    if (P >= LANE_KERNEL_MIN && s <= LANE_SMEM_MAX) {
-        static std::once_flag once;
-        std::call_once(once, [] {
-            cudaFuncSetAttribute(leaf_lane_smem_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-            cudaFuncSetAttribute(leaf_lane_smem_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        });
-        const int T = (s + 7) / 8;
-        const size_t per_warp = (size_t)(square ? 1 : 2) * 8 * T * 33 * 4;
-        const int wpb = 2;
-        const long warps = (P + 31) / 32;
-        const unsigned grid = (unsigned)((warps + wpb - 1) / wpb);
-        if (square)
-            leaf_lane_smem_kernel<true><<<grid, 32 * wpb, wpb * per_warp, st>>>(A, lda, Bm, ldb, OUT, ldo, s, P);
-        else
-            leaf_lane_smem_kernel<false><<<grid, 32 * wpb, wpb * per_warp, st>>>(A, lda, Bm, ldb, OUT, ldo, s, P);
-        return cudaGetLastError();
-    }
     if (P >= LANE_KERNEL_MIN) {
         const bool vec = ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(Bm)) & 15u) == 0 &&
                          lda % 4 == 0 && ldb % 4 == 0;

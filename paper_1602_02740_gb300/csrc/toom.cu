@@ -7,7 +7,9 @@
 //
 // Points (Section 6): x = 0 and x = +-2^j, j = 0..n-1, stored in the order
 // 0, +1, -1, +2, -2, ...; signed values are sign-magnitude.
+#include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "tc_device.cuh"
 #include "tc_internal.h"
@@ -825,10 +827,10 @@ interp_warp_kernel(InterpArgs a, DivTable dt, long P) {
 // memory (many products, long values).
 //
 // Every chain of the even-odd combine and of both Newton loops reads its
-// operands from low limbs to high, carrying a borrow, a division remainder and
-// a few limbs of look-behind, so one warp can push a 32 KL-limb window through
-// all of them before moving on: the values live in shared memory one window
-// at a time and the work buffer is touched a fixed number of times instead of
+// operands from low limbs to high, carrying a borrow, a remainder or a few
+// limbs of look-behind, so one warp can push a 32 KL-limb window through all
+// of them before moving on: the values live in shared memory one window at a
+// time and the work buffer is touched a fixed number of times instead of
 // once per chain.
 //
 // Pass A (even-odd combine, Section 4, and Theorem 3.2): a right shift by R
@@ -837,6 +839,17 @@ interp_warp_kernel(InterpArgs a, DivTable dt, long P) {
 // after stage kk).  Every chain of stage kk reads values written by stage
 // kk - 1, so offsets agree within a stage; c_m is final after stage m, at
 // offset 2(m + 1), and is written to the work buffer at its true position.
+//
+// The odd divisors of Theorem 3.2 are deferred: stage kk keeps
+// c'_m = c_m d_1 ... d_kk for m > kk (no division), and the one chain that
+// meets operands of different scale, m = kk, multiplies c'_(kk-1) by
+// d_(kk-1) first.  So c'_m = c_m d_1 ... d_(m-1) when c_m is final, and it is
+// divided then, by products of consecutive d_j grouped below 2^31: n(n-1)/2
+// divisions become a few per node (21 instead of 55 for n = 11).  Every
+// shift stays exact (the scale factors are odd) and every intermediate stays
+// non-negative; the scaled values are up to n(n-1) bits longer, which the
+// step count covers.
+//
 // Pass B (Theorem 3.3) re-reads the final Newton coefficients with aligned
 // windows; its left shifts only look behind.  Pass C recomposes.
 // ---------------------------------------------------------------------------
@@ -855,20 +868,55 @@ __device__ __forceinline__ void look_behind(const u32 x[KL], const u32 h[NB], u3
     for (int j = 0; j < KL; ++j) e[NB + j] = x[j];
 }
 
-// Per-warp shared memory: value windows c_1..c_n of both polynomials plus
-// ce_0 (co_0 = 0 is not stored), the even-odd chain states (8 words per
-// node) and the Newton chain states (loop 1: 8 words per chain, both
-// polynomials; loop 2 reuses the space, 6 words per chain).
-struct StreamLayout {
-    int vals, st0, st1, words;
+// y = x f for a streamed value x and f < 2^31: limb j of y is lo(x_j f) +
+// hi(x_(j-1) f) + carry, with the carry 0 or 1.  hi_in: hi(f x) of the limb
+// below the chunk; carry: into the chunk (both updated, warp-uniform).
+template <int KL>
+__device__ __forceinline__ void warp_mul_small(const u32 x[KL], u32 f, u32& hi_in, u32& carry,
+                                               u32 y[KL]) {
+    u32 lo[KL], hi[KL], sh[KL];
+#pragma unroll
+    for (int j = 0; j < KL; ++j) {
+        lo[j] = x[j] * f;
+        hi[j] = __umulhi(x[j], f);
+    }
+    const u32 hp = __shfl_up_sync(FULL, hi[KL - 1], 1);
+    sh[0] = lane_id() == 0 ? hi_in : hp;
+#pragma unroll
+    for (int j = 1; j < KL; ++j) sh[j] = hi[j - 1];
+    warp_add_seg<KL>(lo, sh, carry, y);
+    hi_in = __shfl_sync(FULL, hi[KL - 1], 31);
+}
+
+// Grouped divisors of the deferred division: the odd factors of d_1, d_2, ...
+// in order, packed greedily into products below 2^31 ("full" groups).  Node m
+// divides by the full groups inside the factors of d_1 .. d_(m-1), then by the
+// product of the factors left over ("part").
+struct FinTable {
+    DivConst full[48];
+    DivConst part[32];
+    unsigned char nfull[32];
+    unsigned char haspart[32];
+    short off[33];  // first remainder slot of node m (both polynomials: 2 words per slot)
 };
 
-__host__ __device__ inline StreamLayout stream_layout(int n, int C) {
+// Per-warp shared memory: value windows c_1..c_n of both polynomials plus
+// ce_0 (co_0 = 0 is not stored), then chain states: even-odd (8 words per
+// node), Newton loop 1 (6 words per chain: 3 per polynomial), the scale
+// multiplications (8 words per node), the deferred divisions (2 words per
+// divisor).  Loop 2 reuses the loop-1 space (6 words per chain).
+struct StreamLayout {
+    int vals, st0, st1, stm, stf, words;
+};
+
+__host__ __device__ inline StreamLayout stream_layout(int n, int C, int fin_slots) {
     StreamLayout L;
     L.vals = (2 * n + 1) * C;
     L.st0 = 8 * (n + 1);
-    L.st1 = 4 * n * (n + 1);
-    L.words = L.vals + L.st0 + L.st1;
+    L.st1 = 3 * n * (n + 1);
+    L.stm = 8 * (n + 1);
+    L.stf = (2 * fin_slots + 3) / 4 * 4;
+    L.words = L.vals + L.st0 + L.st1 + L.stm + L.stf;
     return L;
 }
 
@@ -885,7 +933,7 @@ __device__ __forceinline__ void st_window(u32* row, int start, int Y, const u32 
 }
 
 __global__ void __launch_bounds__(256)
-interp_stream_kernel(InterpArgs a, DivTable dt, long P) {
+interp_stream_kernel(InterpArgs a, DivTable dt, FinTable ft, long P) {
     constexpr int KL = 4, C = 32 * KL;
     extern __shared__ __align__(16) u32 sm[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -895,10 +943,12 @@ interp_stream_kernel(InterpArgs a, DivTable dt, long P) {
     const LevelGeom& g = a.g;
     const int n = g.n, Y = g.Y, len = 2 * g.e;
     const int npts = 2 * g.B - 1;
-    const StreamLayout L = stream_layout(n, C);
+    const StreamLayout L = stream_layout(n, C, ft.off[n + 1]);
     u32* vals = sm + (long)warp * L.words;
     u32* st0 = vals + L.vals;
     u32* st1 = st0 + L.st0;
+    u32* stm = st1 + L.st1;
+    u32* stf = stm + L.stm;
     u32* W = a.work + k * (long)(2 * (n + 1)) * Y;
     // this lane's limbs of the window of c_m (m >= 1) or ce_0 (p = 0, m = 0)
     auto V = [&](int p, int m) -> u32* {
@@ -918,11 +968,12 @@ interp_stream_kernel(InterpArgs a, DivTable dt, long P) {
     };
     u32 negmask = 0;  // bit m: |W(-2^(m-1))| was negated
     for (int m = 1; m <= n; ++m) negmask |= sgn(2 * m) ? 1u << m : 0u;
-    for (int i = lane; i < L.st0 + L.st1; i += 32) st0[i] = 0;
+    for (int i = lane; i < L.st0 + L.st1 + L.stm + L.stf; i += 32) st0[i] = 0;
     __syncwarp();
 
     // ---- pass A: even-odd combine and Newton loop 1 ----
-    const int stepsA = (Y + 2 * n + 2 + C - 1) / C;
+    const int grow = (n * (n - 1) + 31) / 32 + 1;  // limbs of the deferred scale factors
+    const int stepsA = (Y + 2 * n + 2 + grow + C - 1) / C;
     for (int step = 0; step < stepsA; ++step) {
         const int base = C * step;  // absolute limb of an offset-0 window
         __syncwarp();
@@ -970,26 +1021,40 @@ interp_stream_kernel(InterpArgs a, DivTable dt, long P) {
                 s[5] = T[KL - 3]; s[6] = T[KL - 2]; s[7] = T[KL - 1];
             }
         }
-        // Theorem 3.2, in place with m descending (each update reads the old c_(m-1))
+        // Theorem 3.2 on the scaled values, in place with m descending (each
+        // update reads the old c'_(m-1))
         int t1 = 0;  // index of chain (kk, kk)
         for (int kk = 1; kk <= n; ++kk) {
             for (int m = n; m >= kk; --m) {
                 const int R = m == kk ? 2 * (m - 1) : 2 * (m - kk - 1);
                 const int q = R >> 5;
                 const u32 r = (u32)(R & 31);
-                const bool div = m > kk;
-                const DivConst& d1 = dt.d[0][div ? kk : 0];
-                const DivConst& d2 = dt.d[1][div ? kk : 0];
-                // per polynomial: 2 limbs of look-behind, first remainder | borrow << 31
-                // (remainders are below d < 2^31), second remainder
-                u32* s = st1 + 8 * (t1 + m - kk);
-                u32 out[2][KL], dtop[2][2], bw[2] = {s[2] >> 31, s[6] >> 31};
+                // scale of c'_(kk-1) to meet c'_kk: d_(kk-1) = f1 f2 (f2 = 1 below k = 16)
+                const u32 f1 = m == kk && kk >= 2 ? dt.d[0][kk - 1].d : 1u;
+                const u32 f2 = m == kk && kk >= 2 ? dt.d[1][kk - 1].d : 1u;
+                u32* s = st1 + 6 * (t1 + m - kk);  // per polynomial: 2 limbs, borrow
+                u32* sm8 = stm + 8 * kk;           // per polynomial: (hi, carry) per factor
+                u32 out[2][KL], dtop[2][2], bw[2] = {s[2], s[5]}, mst[2][4];
 #pragma unroll
                 for (int p = 0; p < 2; ++p) {
                     u32 x[KL], z[KL] = {0, 0, 0, 0}, dv[KL], e[KL + 2];
                     ldv(V(p, m), x);
                     if (m > 1 || p == 0) ldv(V(p, m - 1), z);
-                    const u32 h[2] = {s[4 * p], s[4 * p + 1]};
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) mst[p][i] = sm8[4 * p + i];
+                    if (f1 > 1) {
+                        u32 zz[KL];
+                        warp_mul_small<KL>(z, f1, mst[p][0], mst[p][1], zz);
+#pragma unroll
+                        for (int j = 0; j < KL; ++j) z[j] = zz[j];
+                    }
+                    if (f2 > 1) {
+                        u32 zz[KL];
+                        warp_mul_small<KL>(z, f2, mst[p][2], mst[p][3], zz);
+#pragma unroll
+                        for (int j = 0; j < KL; ++j) z[j] = zz[j];
+                    }
+                    const u32 h[2] = {s[3 * p], s[3 * p + 1]};
                     warp_sub_seg<KL>(x, z, bw[p], dv);
                     look_behind<KL, 2>(dv, h, e);
 #pragma unroll
@@ -998,34 +1063,38 @@ interp_stream_kernel(InterpArgs a, DivTable dt, long P) {
                     dtop[p][0] = dv[KL - 2];
                     dtop[p][1] = dv[KL - 1];
                 }
-                u32 B1[2] = {s[2] & 0x7fffffffu, s[6] & 0x7fffffffu}, B2[2] = {s[3], s[7]};
-                if (d1.d > 1) {
-#pragma unroll
-                    for (int p = 0; p < 2; ++p) warp_exact_div_seg<KL>(out[p], d1, B1[p]);
-                }
-                if (d2.d > 1) {
-#pragma unroll
-                    for (int p = 0; p < 2; ++p) warp_exact_div_seg<KL>(out[p], d2, B2[p]);
-                }
 #pragma unroll
                 for (int p = 0; p < 2; ++p) st_seg<KL>(V(p, m), out[p]);
                 __syncwarp();
                 if (lane == 0) {
-                    s[2] = B1[0] | bw[0] << 31; s[3] = B2[0];
-                    s[6] = B1[1] | bw[1] << 31; s[7] = B2[1];
+                    s[2] = bw[0]; s[5] = bw[1];
+                    if (f1 > 1) {
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) { sm8[i] = mst[0][i]; sm8[4 + i] = mst[1][i]; }
+                    }
                 }
                 if (lane == 31) {
                     s[0] = dtop[0][0]; s[1] = dtop[0][1];
-                    s[4] = dtop[1][0]; s[5] = dtop[1][1];
+                    s[3] = dtop[1][0]; s[4] = dtop[1][1];
                 }
             }
             t1 += n - kk + 1;
-            // c_kk is final, at offset 2 kk + 2
-            u32 v[KL];
-            ldv(V(0, kk), v);
-            st_window<KL>(Wrow(0, kk), base - 2 * kk - 2, Y, v);
-            ldv(V(1, kk), v);
-            st_window<KL>(Wrow(1, kk), base - 2 * kk - 2, Y, v);
+            // c'_kk is final, at offset 2 kk + 2: divide by d_1 ... d_(kk-1) and store
+            u32 v[2][KL];
+            ldv(V(0, kk), v[0]);
+            ldv(V(1, kk), v[1]);
+            u32* sf = stf + 2 * ft.off[kk];
+            const int nf = ft.nfull[kk] + ft.haspart[kk];
+            for (int i = 0; i < nf; ++i) {
+                const DivConst& dc = i < ft.nfull[kk] ? ft.full[i] : ft.part[kk];
+                u32 B[2] = {sf[2 * i], sf[2 * i + 1]};
+                warp_exact_div_seg<KL>(v[0], dc, B[0]);
+                warp_exact_div_seg<KL>(v[1], dc, B[1]);
+                __syncwarp();
+                if (lane == 0) { sf[2 * i] = B[0]; sf[2 * i + 1] = B[1]; }
+            }
+            st_window<KL>(Wrow(0, kk), base - 2 * kk - 2, Y, v[0]);
+            st_window<KL>(Wrow(1, kk), base - 2 * kk - 2, Y, v[1]);
         }
     }
     __syncwarp();
@@ -1118,6 +1187,57 @@ interp_stream_kernel(InterpArgs a, DivTable dt, long P) {
     }
 }
 
+// Grouping of the deferred divisors for degree n (see the streaming kernel).
+static FinTable make_fin_table(int n, int KL) {
+    FinTable f;
+    memset(&f, 0, sizeof(f));
+    // odd factors of d_1 .. d_(n-1), with the node after whose d_j each ends
+    std::vector<u32> fac;
+    std::vector<int> upto;  // fac[i] belongs to d_(upto[i])
+    for (int j = 1; j <= n - 1; ++j) {
+        if (j < 16) {
+            fac.push_back((u32)((1ull << (2 * j)) - 1));
+            upto.push_back(j);
+        } else {
+            fac.push_back((u32)((1ull << j) - 1));
+            upto.push_back(j);
+            fac.push_back((u32)((1ull << j) + 1));
+            upto.push_back(j);
+        }
+    }
+    // greedy groups below 2^31
+    std::vector<int> gstart;
+    std::vector<u64> gprod;
+    for (size_t i = 0; i < fac.size(); ++i) {
+        if (gprod.empty() || gprod.back() * fac[i] >= (1ull << 31)) {
+            gstart.push_back((int)i);
+            gprod.push_back(fac[i]);
+        } else {
+            gprod.back() *= fac[i];
+        }
+    }
+    for (size_t i = 0; i < gprod.size() && i < 48; ++i) f.full[i] = make_div((u32)gprod[i], KL);
+    int slot = 0;
+    for (int m = 0; m <= n; ++m) {
+        f.off[m] = (short)slot;
+        // factors of d_1 .. d_(m-1)
+        size_t cnt = 0;
+        while (cnt < fac.size() && upto[cnt] <= m - 1) ++cnt;
+        int full = 0;
+        while (full < (int)gstart.size() &&
+               (full + 1 < (int)gstart.size() ? (size_t)gstart[full + 1] : fac.size()) <= cnt)
+            ++full;
+        u64 part = 1;
+        for (size_t i = full < (int)gstart.size() ? (size_t)gstart[full] : cnt; i < cnt; ++i) part *= fac[i];
+        f.nfull[m] = (unsigned char)full;
+        f.haspart[m] = part > 1 ? 1 : 0;
+        if (part > 1) f.part[m] = make_div((u32)part, KL);
+        slot += full + f.haspart[m];
+    }
+    f.off[n + 1] = (short)slot;
+    return f;
+}
+
 // Kernel choice for a level: many products -> one warp per product (values in
 // shared memory when they fit, else in the work buffer); few products -> one
 // block per product.
@@ -1155,7 +1275,13 @@ cudaError_t launch_interp(const LevelGeom& g, const u32* y, const uint8_t* su, c
         if (!a.use_smem) {
             // long values: stream windows through shared memory; pick the warps per
             // block that keep the most warps resident (1 KB reserved per block)
-            const int per_warp = stream_layout(g.n, 128).words * 4;
+            static FinTable fins[32];
+            static std::once_flag fin_once;
+            std::call_once(fin_once, [] {
+                for (int nn = 1; nn < 32; ++nn) fins[nn] = make_fin_table(nn, 4);
+            });
+            const FinTable& ft = fins[g.n];
+            const int per_warp = stream_layout(g.n, 128, ft.off[g.n + 1]).words * 4;
             int best_w = 1, best_res = 0;
             for (int w = 1; w <= 8; ++w) {
                 if (w * per_warp > STREAM_SMEM_MAX) break;
@@ -1172,7 +1298,7 @@ cudaError_t launch_interp(const LevelGeom& g, const u32* y, const uint8_t* su, c
                                      STREAM_SMEM_MAX);
             });
             const long grid = (P + best_w - 1) / best_w;
-            interp_stream_kernel<<<(unsigned)grid, best_w * 32, (size_t)best_w * per_warp, st>>>(a, dt, P);
+            interp_stream_kernel<<<(unsigned)grid, best_w * 32, (size_t)best_w * per_warp, st>>>(a, dt, ft, P);
             return cudaGetLastError();
         }
         int wpb = a.use_smem ? (int)((96 * 1024) / warp_smem) : 4;

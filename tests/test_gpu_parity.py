@@ -221,9 +221,9 @@ def test_batch_mixed_sizes(ctx, tc):
 
 
 # ---------------------------------------------------------------- base case, large batches
-# 4096 or more products select the lane-per-product kernels: one lane per
-# product up to 136 limbs, a lane pair per product (rows in shared memory)
-# up to 792 limbs, one lane per product from global memory beyond.
+# 4096 or more products select the lane-per-product kernels: a lane pair per
+# product (rows in shared memory) up to 792 limbs, one lane per product from
+# global memory beyond.
 
 @pytest.mark.parametrize("L", [1, 3, 7, 8, 9, 31, 63, 64, 65, 88, 100, 128, 137, 184, 200, 224,
                                300, 511, 800])
