@@ -236,28 +236,91 @@ __device__ __forceinline__ void ld_seg_masked(const u32* row, int pos, int len, 
     for (int j = 0; j < KL; j += 4) ld4_masked(row, pos + j, len, v + j);
 }
 
+// Four-limb carry chains in PTX: r = a + b + cin (cin 0 or 1) returning the
+// carry out, r = a - b - bin returning the borrow out, and r += c / r -= c for
+// c in {0, 1}.  The incoming carry enters the flag through cin + (2^32 - 1).
+__device__ __forceinline__ u32 add4c(const u32* a, const u32* b, u32 cin, u32* r) {
+    u32 c, t;
+    asm("add.cc.u32 %5, %6, -1;\n\t"
+        "addc.cc.u32 %0, %7, %11;\n\t"
+        "addc.cc.u32 %1, %8, %12;\n\t"
+        "addc.cc.u32 %2, %9, %13;\n\t"
+        "addc.cc.u32 %3, %10, %14;\n\t"
+        "addc.u32 %4, 0, 0;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(c), "=r"(t)
+        : "r"(cin), "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]), "r"(b[2]),
+          "r"(b[3]));
+    (void)t;
+    return c;
+}
+
+__device__ __forceinline__ u32 sub4b(const u32* a, const u32* b, u32 bin, u32* r) {
+    u32 c, t;
+    asm("sub.cc.u32 %5, 0, %6;\n\t"
+        "subc.cc.u32 %0, %7, %11;\n\t"
+        "subc.cc.u32 %1, %8, %12;\n\t"
+        "subc.cc.u32 %2, %9, %13;\n\t"
+        "subc.cc.u32 %3, %10, %14;\n\t"
+        "subc.u32 %4, 0, 0;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(c), "=r"(t)
+        : "r"(bin), "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]), "r"(b[2]),
+          "r"(b[3]));
+    (void)t;
+    return c & 1u;
+}
+
+__device__ __forceinline__ u32 inc4(u32* r, u32 c) {
+    u32 o;
+    asm("add.cc.u32 %0, %0, %5;\n\t"
+        "addc.cc.u32 %1, %1, 0;\n\t"
+        "addc.cc.u32 %2, %2, 0;\n\t"
+        "addc.cc.u32 %3, %3, 0;\n\t"
+        "addc.u32 %4, 0, 0;"
+        : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "=r"(o)
+        : "r"(c));
+    return o;
+}
+
+__device__ __forceinline__ u32 dec4(u32* r, u32 c) {
+    u32 o;
+    asm("sub.cc.u32 %0, %0, %5;\n\t"
+        "subc.cc.u32 %1, %1, 0;\n\t"
+        "subc.cc.u32 %2, %2, 0;\n\t"
+        "subc.cc.u32 %3, %3, 0;\n\t"
+        "subc.u32 %4, 0, 0;"
+        : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "=r"(o)
+        : "r"(c));
+    return o & 1u;
+}
+
+// r = a + b + cin over KL limbs (KL a multiple of 4); returns the carry out.
 template <int KL>
 __device__ __forceinline__ u32 add_seg(const u32 a[KL], const u32 b[KL], u32 cin, u32 r[KL]) {
-    u64 c = cin;
+    u32 c = cin;
 #pragma unroll
-    for (int j = 0; j < KL; ++j) {
-        const u64 t = (u64)a[j] + b[j] + c;
-        r[j] = (u32)t;
-        c = t >> 32;
-    }
-    return (u32)c;
+    for (int j = 0; j < KL; j += 4) c = add4c(a + j, b + j, c, r + j);
+    return c;
+}
+
+// r = a - b - bin over KL limbs; returns the borrow out.
+template <int KL>
+__device__ __forceinline__ u32 sub_seg(const u32 a[KL], const u32 b[KL], u32 bin, u32 r[KL]) {
+    u32 c = bin;
+#pragma unroll
+    for (int j = 0; j < KL; j += 4) c = sub4b(a + j, b + j, c, r + j);
+    return c;
 }
 
 template <int KL>
-__device__ __forceinline__ u32 sub_seg(const u32 a[KL], const u32 b[KL], u32 bin, u32 r[KL]) {
-    u64 bw = bin;
+__device__ __forceinline__ void inc_seg(u32 r[KL], u32 c) {
 #pragma unroll
-    for (int j = 0; j < KL; ++j) {
-        const u64 t = (u64)a[j] - b[j] - bw;
-        r[j] = (u32)t;
-        bw = (t >> 32) & 1u;
-    }
-    return (u32)bw;
+    for (int j = 0; j < KL; j += 4) c = inc4(r + j, c);
+}
+
+template <int KL>
+__device__ __forceinline__ void dec_seg(u32 r[KL], u32 c) {
+#pragma unroll
+    for (int j = 0; j < KL; j += 4) c = dec4(r + j, c);
 }
 
 template <int KL>
@@ -276,13 +339,16 @@ __device__ __forceinline__ bool ones_seg(const u32 r[KL]) {
     return x == FULL;
 }
 
+// Warp-wide add of two chunks of 32 KL limbs: each lane adds its KL limbs
+// with carry-in 0, the lanes' carries are resolved by one lookahead, and the
+// lanes that receive a carry increment their sum.
 template <int KL>
 __device__ __forceinline__ void warp_add_seg(const u32 a[KL], const u32 b[KL], u32& carry, u32 r[KL]) {
     const u32 g = add_seg<KL>(a, b, 0u, r);
     const bool p = !g && ones_seg<KL>(r);
     u32 cout;
     const u32 cin = warp_carry_scan(g != 0u, p, carry, &cout);
-    if (cin) add_seg<KL>(a, b, 1u, r);
+    inc_seg<KL>(r, cin);
     carry = cout;
 }
 
@@ -292,7 +358,7 @@ __device__ __forceinline__ void warp_sub_seg(const u32 a[KL], const u32 b[KL], u
     const bool p = !g && zero_seg<KL>(r);
     u32 bout;
     const u32 bin = warp_carry_scan(g != 0u, p, borrow, &bout);
-    if (bin) sub_seg<KL>(a, b, 1u, r);
+    dec_seg<KL>(r, bin);
     borrow = bout;
 }
 
