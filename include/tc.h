@@ -155,7 +155,8 @@ tc_status tc_schoolbook(size_t count, size_t limbs, const uint32_t *A, size_t ld
  * 0, +1, -1, +2, -2, ..., +2^(B-2), -2^(B-2).  Value p of row k is written
  * as a magnitude of `estride` limbs at OUT + (k*(2B-1) + p) * estride, and
  * its sign (1 = negative) at SGN[k*(2B-1) + p].  estride must be >= e (the
- * evaluation length) and a multiple of 4.
+ * evaluation length) and a multiple of 4, and OUT 16-byte aligned (the
+ * kernels store 4 limbs at a time); otherwise TC_EINVAL.
  */
 tc_status tc_toom_evaluate(size_t count, size_t limbs, int B, const uint32_t *U, size_t ld,
                            uint32_t *OUT, size_t estride, uint8_t *SGN, void *stream);
@@ -169,7 +170,8 @@ tc_status tc_toom_evaluate(size_t count, size_t limbs, int B, const uint32_t *U,
  * SGN_U[k*(2B-1)+p] xor SGN_V[k*(2B-1)+p] (either may be NULL = all
  * positive); 2*limbs result limbs are written at OUT + k*ldo.  `work` is
  * device scratch of tc_toom_interpolate_work_bytes(count, limbs, B) bytes (may
- * be NULL when that is 0).  ystride >= 2e, multiple of 4.
+ * be NULL when that is 0).  ystride >= 2e, multiple of 4; Y and work
+ * 16-byte aligned (4-limb loads and stores); otherwise TC_EINVAL.
  */
 tc_status tc_toom_interpolate(size_t count, size_t limbs, int B,
                               const uint32_t *Y, size_t ystride,

@@ -602,7 +602,8 @@ extern "C" tc_status tc_toom_evaluate(size_t count, size_t limbs, int B, const u
     if (!U || !OUT || !SGN || B < 2 || B > 32 || limbs == 0 || limbs > (1u << 30))
         return TC_EINVAL;
     LevelGeom g = make_level((int)limbs, B);
-    if (estride < (size_t)g.e || estride % 4) return TC_EINVAL;
+    if (estride < (size_t)g.e || estride % 4 || (reinterpret_cast<uintptr_t>(OUT) & 15u))
+        return TC_EINVAL;
     if (count > 1 && ld < limbs) return TC_EINVAL;
     g.estride = (int)estride;
     CK(launch_eval(U, (long)ld, g, OUT, SGN, (long)count, nullptr, (cudaStream_t)stream));
@@ -622,6 +623,8 @@ extern "C" tc_status tc_toom_interpolate(size_t count, size_t limbs, int B, cons
     if (!Y || !OUT || B < 2 || B > 32 || limbs == 0 || limbs > (1u << 30)) return TC_EINVAL;
     LevelGeom g = make_level((int)limbs, B);
     if (ystride < (size_t)(2 * g.e) || ystride % 4) return TC_EINVAL;
+    if (((reinterpret_cast<uintptr_t>(Y) | reinterpret_cast<uintptr_t>(work)) & 15u) != 0)
+        return TC_EINVAL;
     if (count > 1 && ldo < 2 * limbs) return TC_EINVAL;
     if (interp_work_bytes(g, (long)count) && !work) return TC_EINVAL;
     g.ystride = (int)ystride;

@@ -52,6 +52,7 @@ extern "C" tc_status tc_toom_interpolate_noalloc(size_t count, size_t limbs, int
     if (!Y || !OUT || B < 2 || B > 32 || limbs == 0 || limbs > (1u << 30)) return TC_EINVAL;
     tc::LevelGeom g = tc::make_level((int)limbs, B);
     if (ystride < (size_t)(2 * g.e) || ystride % 4) return TC_EINVAL;
+    if (reinterpret_cast<uintptr_t>(Y) & 15u) return TC_EINVAL;
     if (count > 1 && ldo < 2 * limbs) return TC_EINVAL;
     g.ystride = (int)ystride;
     const size_t need = count * tc::interp_work_bytes(g, (long)count);

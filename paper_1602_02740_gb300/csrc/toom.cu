@@ -913,7 +913,8 @@ __host__ __device__ inline StreamLayout stream_layout(int n, int C, int fin_slot
     StreamLayout L;
     L.vals = (2 * n + 1) * C;
     L.st0 = 8 * (n + 1);
-    L.st1 = 3 * n * (n + 1);
+    L.st1 = (3 * n * (n + 1) + 3) / 4 * 4;  // every region a multiple of 4 words: the value
+                                           // windows of the next warp stay 16-byte aligned
     L.stm = 8 * (n + 1);
     L.stf = (2 * fin_slots + 3) / 4 * 4;
     L.words = L.vals + L.st0 + L.st1 + L.stm + L.stf;

@@ -264,7 +264,8 @@ def test_square_lane_kernel(tc, L):
 # values over 24 KB per product ((4, 2000) onward) take the streaming kernel; (20, 4000) has
 # right shifts of 32 bits or more, (32, 3000) two divisors per Newton step
 @pytest.mark.parametrize("B,L", [(2, 9), (3, 100), (4, 259), (8, 130), (3, 2), (4, 2000), (8, 2055),
-                                 (12, 6000), (20, 4000), (32, 3000)])
+                                 (12, 6000), (20, 4000), (32, 3000),
+                                 (2, 5000), (3, 4000), (6, 3000), (7, 4000), (10, 3000)])
 def test_interpolate_many_products(tc, B, L):
     import torch
     count = 2100
