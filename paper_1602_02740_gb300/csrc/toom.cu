@@ -1239,6 +1239,197 @@ static FinTable make_fin_table(int n, int KL) {
     return f;
 }
 
+// ---------------------------------------------------------------------------
+// Register-resident warp-per-product interpolation for short values
+// (Y <= 32 KL, degree n small): each lane holds KL limbs of every value, so a
+// whole value is one warp chunk and every chain of Section 4 / Theorems 3.2
+// and 3.3 is a single warp operation with no carried state; shifts take the
+// neighbouring lane's limbs by shuffle (right shifts look one lane up, left
+// shifts one lane down).  The values go to shared memory only for the
+// recomposition.
+// ---------------------------------------------------------------------------
+template <int KL>
+__device__ __forceinline__ void shr_chunk(const u32 x[KL], u32 r, u32 out[KL]) {
+    // out = x >> r (r < 32) over the whole warp chunk; the top lane's limb above is 0
+    const u32 up = __shfl_down_sync(FULL, x[0], 1);
+    const u32 above = lane_id() == 31 ? 0u : up;
+#pragma unroll
+    for (int j = 0; j < KL; ++j) out[j] = fshr(x[j], j + 1 < KL ? x[j + 1] : above, r);
+}
+
+template <int KL>
+__device__ __forceinline__ void shl_chunk(const u32 x[KL], u32 s, u32 out[KL]) {
+    // out = x << s (s < 32), truncated to the chunk; the bottom lane's limb below is 0
+    const u32 dn = __shfl_up_sync(FULL, x[KL - 1], 1);
+    const u32 below = lane_id() == 0 ? 0u : dn;
+#pragma unroll
+    for (int j = 0; j < KL; ++j) out[j] = fshl(j > 0 ? x[j - 1] : below, x[j], s);
+}
+
+template <int KL, int N>
+__global__ void __launch_bounds__(256)
+interp_reg_kernel(InterpArgs a, DivTable dt, long P) {
+    extern __shared__ __align__(16) u32 sm[];
+    constexpr int C = 32 * KL;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wpb = blockDim.x >> 5;
+    const long k = (long)blockIdx.x * wpb + warp;
+    if (k >= P) return;  // warp-uniform
+    const LevelGeom& g = a.g;
+    const int npts = 2 * N + 1, len = 2 * g.e;
+    const u32* yk = a.y + k * npts * (long)g.ystride;
+    auto sgn = [&](int p) -> bool {
+        bool s = false;
+        if (a.su) s ^= a.su[k * npts + p] != 0;
+        if (a.sv) s ^= a.sv[k * npts + p] != 0;
+        return s;
+    };
+    u32 c[2][N + 1][KL];
+    // ---- even-odd combine (eq. 4.5-4.6) ----
+    ld_seg_masked<KL>(yk, KL * lane, len, c[0][0]);
+#pragma unroll
+    for (int j = 0; j < KL; ++j) c[1][0][j] = 0;
+#pragma unroll
+    for (int m = 1; m <= N; ++m) {
+        u32 pv[KL], qv[KL], A[KL], D[KL];
+        ld_seg_masked<KL>(yk + (2 * m - 1) * (long)g.ystride, KL * lane, len, pv);
+        ld_seg_masked<KL>(yk + (2 * m) * (long)g.ystride, KL * lane, len, qv);
+        u32 z = 0;
+        warp_add_seg<KL>(pv, qv, z, A);
+        z = 0;
+        warp_sub_seg<KL>(pv, qv, z, D);
+        const bool ng = sgn(2 * m);
+        u32 S[KL], T[KL];
+#pragma unroll
+        for (int j = 0; j < KL; ++j) { S[j] = ng ? D[j] : A[j]; T[j] = ng ? A[j] : D[j]; }
+        shr_chunk<KL>(S, 1, c[0][m]);
+        if (m == 1) shr_chunk<KL>(T, 1, c[1][m]);
+        else shl_chunk<KL>(T, (u32)(m - 2), c[1][m]);
+    }
+    // ---- Theorem 3.2, in place with m descending ----
+#pragma unroll
+    for (int kk = 1; kk <= N; ++kk) {
+#pragma unroll
+        for (int m = N; m >= kk; --m) {
+            const u32 R = (u32)(m == kk ? 2 * (m - 1) : 2 * (m - kk - 1));
+#pragma unroll
+            for (int p = 0; p < 2; ++p) {
+                u32 dv[KL], z = 0;
+                warp_sub_seg<KL>(c[p][m], c[p][m - 1], z, dv);
+                shr_chunk<KL>(dv, R, c[p][m]);
+            }
+            if (m > kk) {
+#pragma unroll
+                for (int p = 0; p < 2; ++p) {
+                    u32 B = 0;
+                    warp_exact_div_seg<KL>(c[p][m], dt.d[0][kk], B);
+                    if (dt.d[1][kk].d > 1) {
+                        B = 0;
+                        warp_exact_div_seg<KL>(c[p][m], dt.d[1][kk], B);
+                    }
+                }
+            }
+        }
+    }
+    // ---- Theorem 3.3, in place with kx ascending ----
+#pragma unroll
+    for (int mm = N - 1; mm >= 1; --mm) {
+#pragma unroll
+        for (int kx = mm; kx <= N - 1; ++kx) {
+#pragma unroll
+            for (int p = 0; p < 2; ++p) {
+                u32 sz[KL], z = 0;
+                shl_chunk<KL>(c[p][kx + 1], (u32)(2 * (mm - 1)), sz);
+                warp_sub_seg<KL>(c[p][kx], sz, z, c[p][kx]);
+            }
+        }
+    }
+    // ---- recompose out[l] = sum_t w_t[l - t b] from shared memory ----
+    u32* sw = sm + (long)warp * 2 * (N + 1) * C;
+#pragma unroll
+    for (int p = 0; p < 2; ++p)
+#pragma unroll
+        for (int m = 0; m <= N; ++m) st_seg<KL>(sw + (p * (N + 1) + m) * C + KL * lane, c[p][m]);
+    __syncwarp();
+    u32* out = a.out + k * a.out_stride;
+    const bool aligned = ((reinterpret_cast<uintptr_t>(out) & 15u) == 0);
+    UnsignedNorm nst{0, 0};
+    const int nterms = 2 * N + 1;
+    for (int base_l = 0; base_l < a.out_len; base_l += CH) {
+        u64 cols[4];
+        const int l0 = base_l + 4 * lane;
+        const int t0 = l0 / g.b;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int l = l0 + j;
+            u64 S = 0;
+            if (l < a.out_len) {
+                int t = t0;
+                while ((t + 1) * g.b <= l) ++t;  // t = floor(l / b)
+                if (t > nterms - 1) t = nterms - 1;
+                for (; t >= 0; --t) {
+                    const int x = l - t * g.b;
+                    if (x >= C) break;
+                    S += sw[((t & 1) * (N + 1) + ((t + 1) >> 1)) * C + x];
+                }
+            }
+            cols[j] = S;
+        }
+        u32 d[4];
+        warp_norm_unsigned(cols, nst, d);
+        if (aligned && l0 + 4 <= a.out_len) {
+            st4(out + l0, d);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (l0 + j < a.out_len) out[l0 + j] = d[j];
+        }
+    }
+}
+
+// Limbs per lane of the register-resident kernel for a level, 0 if none applies.
+static int reg_interp_kl(const LevelGeom& g) {
+    const int n = g.n;
+    if (n <= 2 && g.Y <= 32 * 16 && g.Y > 32 * 12) return 16;
+    if (n <= 3 && g.Y <= 32 * 12 && g.Y > 32 * 8) return 12;
+    if (n <= 5 && g.Y <= 32 * 8) return 8;
+    return 0;
+}
+
+template <int KL, int N>
+static cudaError_t launch_reg_interp(const InterpArgs& a, long P, cudaStream_t st) {
+    static const DivTable dtk = make_div_table(KL);
+    const size_t per_warp = (size_t)2 * (N + 1) * 32 * KL * 4;
+    int wpb = (int)((96 * 1024) / per_warp);
+    if (wpb > 8) wpb = 8;
+    if (wpb < 1) wpb = 1;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaFuncSetAttribute(interp_reg_kernel<KL, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             200 * 1024);
+    });
+    const long grid = (P + wpb - 1) / wpb;
+    interp_reg_kernel<KL, N><<<(unsigned)grid, wpb * 32, wpb * per_warp, st>>>(a, dtk, P);
+    return cudaGetLastError();
+}
+
+static cudaError_t launch_reg_interp_kl(int kl, const InterpArgs& a, long P, cudaStream_t st) {
+    const int n = a.g.n;
+    if (kl == 16) return n == 1 ? launch_reg_interp<16, 1>(a, P, st) : launch_reg_interp<16, 2>(a, P, st);
+    if (kl == 12) {
+        if (n == 1) return launch_reg_interp<12, 1>(a, P, st);
+        if (n == 2) return launch_reg_interp<12, 2>(a, P, st);
+        return launch_reg_interp<12, 3>(a, P, st);
+    }
+    switch (n) {
+        case 1: return launch_reg_interp<8, 1>(a, P, st);
+        case 2: return launch_reg_interp<8, 2>(a, P, st);
+        case 3: return launch_reg_interp<8, 3>(a, P, st);
+        case 4: return launch_reg_interp<8, 4>(a, P, st);
+        default: return launch_reg_interp<8, 5>(a, P, st);
+    }
+}
+
 // Kernel choice for a level: many products -> one warp per product (values in
 // shared memory when they fit, else in the work buffer); few products -> one
 // block per product.
@@ -1252,6 +1443,7 @@ constexpr size_t BLOCK_SMEM_MAX = 160 * 1024;
 
 size_t interp_work_bytes(const LevelGeom& g, long P) {
     if (use_wide(g, P)) return (wide_work_bytes(g, P) + P - 1) / P;  // per product, rounded up
+    if (use_warp_kernel(g, P) && reg_interp_kl(g)) return 0;
     if (use_warp_kernel(g, P)) return warp_values_bytes(g) <= WARP_SMEM_MAX ? 0 : warp_values_bytes(g);
     return block_values_bytes(g) <= BLOCK_SMEM_MAX ? 0 : block_values_bytes(g);
 }
@@ -1267,6 +1459,12 @@ cudaError_t launch_interp(const LevelGeom& g, const u32* y, const uint8_t* su, c
     static const DivTable dt4 = make_div_table(4), dt8 = make_div_table(8);
     const DivTable& dt = dt4;
     // many products: one warp per product
+    if (use_warp_kernel(g, P) && reg_interp_kl(g)) {
+        InterpArgs a;
+        a.g = g; a.y = y; a.su = su; a.sv = sv; a.out = out; a.out_stride = out_stride;
+        a.out_len = out_len; a.work = nullptr; a.use_smem = 1;
+        return launch_reg_interp_kl(reg_interp_kl(g), a, P, st);
+    }
     if (use_warp_kernel(g, P)) {
         const size_t warp_smem = warp_values_bytes(g);
         InterpArgs a;

@@ -262,10 +262,13 @@ def test_square_lane_kernel(tc, L):
 # 2048 or more products with small values select the warp-per-product kernel.
 
 # values over 24 KB per product ((4, 2000) onward) take the streaming kernel; (20, 4000) has
-# right shifts of 32 bits or more, (32, 3000) two divisors per Newton step
+# right shifts of 32 bits or more, (32, 3000) two divisors per Newton step.  Short values of
+# small degree ((2, 9), (3, 100), (4, 259), (3, 2) and the last six) take the register-resident
+# kernel with 8, 12 or 16 limbs per lane.
 @pytest.mark.parametrize("B,L", [(2, 9), (3, 100), (4, 259), (8, 130), (3, 2), (4, 2000), (8, 2055),
                                  (12, 6000), (20, 4000), (32, 3000),
-                                 (2, 5000), (3, 4000), (6, 3000), (7, 4000), (10, 3000)])
+                                 (2, 5000), (3, 4000), (6, 3000), (7, 4000), (10, 3000),
+                                 (3, 450), (3, 650), (2, 400), (4, 600), (6, 500), (5, 400)])
 def test_interpolate_many_products(tc, B, L):
     import torch
     count = 2100
