@@ -240,32 +240,32 @@ __device__ __forceinline__ void ld_seg_masked(const u32* row, int pos, int len, 
 // carry out, r = a - b - bin returning the borrow out, and r += c / r -= c for
 // c in {0, 1}.  The incoming carry enters the flag through cin + (2^32 - 1).
 __device__ __forceinline__ u32 add4c(const u32* a, const u32* b, u32 cin, u32* r) {
-    u32 c, t;
-    asm("add.cc.u32 %5, %6, -1;\n\t"
-        "addc.cc.u32 %0, %7, %11;\n\t"
-        "addc.cc.u32 %1, %8, %12;\n\t"
-        "addc.cc.u32 %2, %9, %13;\n\t"
-        "addc.cc.u32 %3, %10, %14;\n\t"
-        "addc.u32 %4, 0, 0;"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(c), "=r"(t)
+    u32 c;
+    asm("{\n\t.reg .u32 t;\n\t"
+        "add.cc.u32 t, %5, -1;\n\t"
+        "addc.cc.u32 %0, %6, %10;\n\t"
+        "addc.cc.u32 %1, %7, %11;\n\t"
+        "addc.cc.u32 %2, %8, %12;\n\t"
+        "addc.cc.u32 %3, %9, %13;\n\t"
+        "addc.u32 %4, 0, 0;\n\t}"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(c)
         : "r"(cin), "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]), "r"(b[2]),
           "r"(b[3]));
-    (void)t;
     return c;
 }
 
 __device__ __forceinline__ u32 sub4b(const u32* a, const u32* b, u32 bin, u32* r) {
-    u32 c, t;
-    asm("sub.cc.u32 %5, 0, %6;\n\t"
-        "subc.cc.u32 %0, %7, %11;\n\t"
-        "subc.cc.u32 %1, %8, %12;\n\t"
-        "subc.cc.u32 %2, %9, %13;\n\t"
-        "subc.cc.u32 %3, %10, %14;\n\t"
-        "subc.u32 %4, 0, 0;"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(c), "=r"(t)
+    u32 c;
+    asm("{\n\t.reg .u32 t;\n\t"
+        "sub.cc.u32 t, 0, %5;\n\t"
+        "subc.cc.u32 %0, %6, %10;\n\t"
+        "subc.cc.u32 %1, %7, %11;\n\t"
+        "subc.cc.u32 %2, %8, %12;\n\t"
+        "subc.cc.u32 %3, %9, %13;\n\t"
+        "subc.u32 %4, 0, 0;\n\t}"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(c)
         : "r"(bin), "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]), "r"(b[2]),
           "r"(b[3]));
-    (void)t;
     return c & 1u;
 }
 
