@@ -379,8 +379,10 @@ cudaError_t launch_schoolbook_big(const u32* A, long lda, const u32* Bm, long ld
 // accumulators, slot k holding column 8D+4h+k.  After diagonal D the odd lane
 // hands its slots 0..7 (columns 8D+4 .. 8D+11, which it will not touch again)
 // to the even lane, which then holds columns 8D .. 8D+7 complete and emits
-// them through a 64-bit running carry; both lanes slide their windows by
-// eight columns.  A final diagonal with no tiles flushes the top columns.
+// them by two carry chains over the eight 96-bit column sums (the overflow
+// past column 8D+7 becomes the next window's column 0); both lanes slide
+// their windows by eight columns.  A final diagonal with no tiles flushes the
+// top columns.
 //
 // Every operand limb is read from global memory once (coalesced, into
 // shared memory).  Rows are staged with a stride of 8 or 24 (mod 32) words,
@@ -406,6 +408,84 @@ __device__ __forceinline__ void add96(u32& lo, u32& mid, u32& hi, u32 a, u32 b, 
         "addc.u32 %2, %2, %5;"
         : "+r"(lo), "+r"(mid), "+r"(hi)
         : "r"(a), "r"(b), "r"(c));
+}
+
+// R[0..10] = sum_(k<8) (lo_k + mid_k 2^32 + hi_k 2^64) 2^(32k): lo plus mid one limb
+// up, then plus hi two limbs up, each one carry chain.
+__device__ __forceinline__ void add8_shifted(const u32* lo, const u32* mid, const u32* hi, u32* R) {
+    R[0] = lo[0];
+    asm("add.cc.u32 %0, %9, %16;\n\t"
+        "addc.cc.u32 %1, %10, %17;\n\t"
+        "addc.cc.u32 %2, %11, %18;\n\t"
+        "addc.cc.u32 %3, %12, %19;\n\t"
+        "addc.cc.u32 %4, %13, %20;\n\t"
+        "addc.cc.u32 %5, %14, %21;\n\t"
+        "addc.cc.u32 %6, %15, %22;\n\t"
+        "addc.cc.u32 %7, %23, 0;\n\t"
+        "addc.u32 %8, 0, 0;"
+        : "=r"(R[1]), "=r"(R[2]), "=r"(R[3]), "=r"(R[4]), "=r"(R[5]), "=r"(R[6]), "=r"(R[7]),
+          "=r"(R[8]), "=r"(R[9])
+        : "r"(lo[1]), "r"(lo[2]), "r"(lo[3]), "r"(lo[4]), "r"(lo[5]), "r"(lo[6]), "r"(lo[7]),
+          "r"(mid[0]), "r"(mid[1]), "r"(mid[2]), "r"(mid[3]), "r"(mid[4]), "r"(mid[5]), "r"(mid[6]),
+          "r"(mid[7]));
+    asm("add.cc.u32 %0, %0, %9;\n\t"
+        "addc.cc.u32 %1, %1, %10;\n\t"
+        "addc.cc.u32 %2, %2, %11;\n\t"
+        "addc.cc.u32 %3, %3, %12;\n\t"
+        "addc.cc.u32 %4, %4, %13;\n\t"
+        "addc.cc.u32 %5, %5, %14;\n\t"
+        "addc.cc.u32 %6, %6, %15;\n\t"
+        "addc.cc.u32 %7, %7, %16;\n\t"
+        "addc.u32 %8, 0, 0;"
+        : "+r"(R[2]), "+r"(R[3]), "+r"(R[4]), "+r"(R[5]), "+r"(R[6]), "+r"(R[7]), "+r"(R[8]),
+          "+r"(R[9]), "=r"(R[10])
+        : "r"(hi[0]), "r"(hi[1]), "r"(hi[2]), "r"(hi[3]), "r"(hi[4]), "r"(hi[5]), "r"(hi[6]),
+          "r"(hi[7]));
+}
+
+// R[0..10] += (x0 + x1 2^32 + x2 2^64) at limb 0 (squaring path: the carry kept apart).
+__device__ __forceinline__ void add3_into11(u32* R, u32 x0, u32 x1, u32 x2) {
+    asm("add.cc.u32 %0, %0, %11;\n\t"
+        "addc.cc.u32 %1, %1, %12;\n\t"
+        "addc.cc.u32 %2, %2, %13;\n\t"
+        "addc.cc.u32 %3, %3, 0;\n\t"
+        "addc.cc.u32 %4, %4, 0;\n\t"
+        "addc.cc.u32 %5, %5, 0;\n\t"
+        "addc.cc.u32 %6, %6, 0;\n\t"
+        "addc.cc.u32 %7, %7, 0;\n\t"
+        "addc.cc.u32 %8, %8, 0;\n\t"
+        "addc.cc.u32 %9, %9, 0;\n\t"
+        "addc.u32 %10, %10, 0;"
+        : "+r"(R[0]), "+r"(R[1]), "+r"(R[2]), "+r"(R[3]), "+r"(R[4]), "+r"(R[5]), "+r"(R[6]),
+          "+r"(R[7]), "+r"(R[8]), "+r"(R[9]), "+r"(R[10])
+        : "r"(x0), "r"(x1), "r"(x2));
+}
+
+// Squaring: R = 2 R + sum_(k<4) a_k^2 2^(64k) over 11 limbs.
+__device__ __forceinline__ void double_add_squares(u32* R, const u32* a) {
+#pragma unroll
+    for (int k = 10; k >= 1; --k) R[k] = fshl(R[k - 1], R[k], 1);
+    R[0] <<= 1;
+    u32 S[8];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        S[2 * k] = a[k] * a[k];
+        S[2 * k + 1] = __umulhi(a[k], a[k]);
+    }
+    asm("add.cc.u32 %0, %0, %11;\n\t"
+        "addc.cc.u32 %1, %1, %12;\n\t"
+        "addc.cc.u32 %2, %2, %13;\n\t"
+        "addc.cc.u32 %3, %3, %14;\n\t"
+        "addc.cc.u32 %4, %4, %15;\n\t"
+        "addc.cc.u32 %5, %5, %16;\n\t"
+        "addc.cc.u32 %6, %6, %17;\n\t"
+        "addc.cc.u32 %7, %7, %18;\n\t"
+        "addc.cc.u32 %8, %8, 0;\n\t"
+        "addc.cc.u32 %9, %9, 0;\n\t"
+        "addc.u32 %10, %10, 0;"
+        : "+r"(R[0]), "+r"(R[1]), "+r"(R[2]), "+r"(R[3]), "+r"(R[4]), "+r"(R[5]), "+r"(R[6]),
+          "+r"(R[7]), "+r"(R[8]), "+r"(R[9]), "+r"(R[10])
+        : "r"(S[0]), "r"(S[1]), "r"(S[2]), "r"(S[3]), "r"(S[4]), "r"(S[5]), "r"(S[6]), "r"(S[7]));
 }
 
 template <bool SQ>
@@ -453,10 +533,9 @@ leaf_pair_kernel(const u32* __restrict__ A, long lda, const u32* __restrict__ Bm
     u32* out = OUT + (p < P ? p : 0) * ldo;
     const bool aligned = ((reinterpret_cast<uintptr_t>(out) & 15u) == 0);
     const int out_len = 2 * s;
-    u32 lo[12], mid[12], hi[12];
+    u32 lo[12], mid[12], hi[12], cin[3] = {0, 0, 0};
 #pragma unroll
     for (int k = 0; k < 12; ++k) { lo[k] = 0; mid[k] = 0; hi[k] = 0; }
-    u64 carry = 0;
     for (int D = 0; D <= 2 * T - 1; ++D) {
         const int Ilo = D - T + 1 > 0 ? D - T + 1 : 0;
         int Ihi = D < T - 1 ? D : T - 1;
@@ -488,38 +567,30 @@ leaf_pair_kernel(const u32* __restrict__ A, long lda, const u32* __restrict__ Bm
             const u32 ph = __shfl_down_sync(FULL, hi[k], 1);
             if (h == 0) add96(lo[k + 4], mid[k + 4], hi[k + 4], pl, pm, ph);
         }
-        if (h == 0) {
-            u32 res[8];
-            uint4 sq = make_uint4(0, 0, 0, 0);
-            if (SQ) sq = ld4(ra + 4 * D);  // a_(4D + k/2) for the even columns (zeros past s)
-            const u32 sq4[4] = {sq.x, sq.y, sq.z, sq.w};
+        // columns 8D .. 8D+7 (even lane): the limbs of sum_k (lo_k + mid_k 2^32 + hi_k 2^64)
+        // 2^(32k), k < 8, by two carry chains.  What spills past column 8D+7 (three
+        // words) is the next diagonal's carry: added into slot 8 (the next window's
+        // column 0), or, when squaring, kept apart because the slots get doubled.
+        u32 R[11];
+        add8_shifted(lo, mid, hi, R);
+        if (SQ) {
+            const uint4 sq = ld4(ra + 4 * D);  // a_(4D + k/2) for the even columns (zeros past s)
+            const u32 sqv[4] = {sq.x, sq.y, sq.z, sq.w};
+            double_add_squares(R, sqv);
+            add3_into11(R, cin[0], cin[1], cin[2]);
+            cin[0] = R[8]; cin[1] = R[9]; cin[2] = R[10];
+        } else if (h == 0) {
+            add96(lo[8], mid[8], hi[8], R[8], R[9], R[10]);
+        }
+        if (emit) {
+            const int c0 = 8 * D;
+            if (aligned && c0 + 8 <= out_len) {
+                st4(out + c0, R);
+                st4(out + c0 + 4, R + 4);
+            } else {
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                u64 vlo = lo[k], vmid = mid[k], vhi = hi[k];
-                if (SQ) {
-                    vhi = (vhi << 1) | (vmid >> 31);
-                    vmid = ((vmid << 1) & 0xffffffffull) | (vlo >> 31);
-                    vlo = (vlo << 1) & 0xffffffffull;
-                    if ((k & 1) == 0) {
-                        const u64 x = (u64)sq4[k / 2] * sq4[k / 2];
-                        vlo += x & 0xffffffffull;
-                        vmid += x >> 32;
-                    }
-                }
-                const u64 t = vlo + (carry & 0xffffffffull);
-                res[k] = (u32)t;
-                carry = (carry >> 32) + (t >> 32) + vmid + (vhi << 32);
-            }
-            if (emit) {
-                const int c0 = 8 * D;
-                if (aligned && c0 + 8 <= out_len) {
-                    st4(out + c0, res);
-                    st4(out + c0 + 4, res + 4);
-                } else {
-#pragma unroll
-                    for (int k = 0; k < 8; ++k)
-                        if (c0 + k < out_len) out[c0 + k] = res[k];
-                }
+                for (int k = 0; k < 8; ++k)
+                    if (c0 + k < out_len) out[c0 + k] = R[k];
             }
         }
 #pragma unroll
