@@ -64,22 +64,32 @@ __device__ __forceinline__ void eval_cols(const u32* row, int s, int B, int b, i
 }
 
 struct EvalCarry {
-    u32 plus;   // carry of E + O into this chunk
     u32 minus;  // borrow of |E - O| into this chunk
+    u32 dtop;   // top limb of O in the previous chunk (the bit that 2 O shifts in)
 };
 
-// Column sums e, o (non-negative) of one chunk -> digits of U(x) = E + O and
-// of |U(-x)| = sign (E - O).  E and O are normalised on their own, then added
-// and subtracted with carry/borrow scans.
+// Column sums e, o (non-negative) of one chunk -> digits of U(x) = E + O and of
+// |U(-x)| = sign (E - O).  E + O is normalised directly; |E - O| is
+// (E + O) - 2 O (sign > 0) or 2 O - (E + O) (sign < 0), so only O is normalised
+// besides, and one borrow scan finishes.
 __device__ __forceinline__ void eval_finish(const u64 e[4], const u64 o[4], int sign,
-                                            UnsignedNorm& ne, UnsignedNorm& no, EvalCarry& cpm,
+                                            UnsignedNorm& np, UnsignedNorm& no, EvalCarry& c,
                                             u32 dp[4], u32 dm[4]) {
-    u32 E[4], O[4];
-    warp_norm_unsigned(e, ne, E);
+    u64 s[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) s[j] = e[j] + o[j];
+    warp_norm_unsigned(s, np, dp);
+    u32 O[4];
     warp_norm_unsigned(o, no, O);
-    warp_add_seg<4>(E, O, cpm.plus, dp);
-    if (sign > 0) warp_sub_seg<4>(E, O, cpm.minus, dm);
-    else warp_sub_seg<4>(O, E, cpm.minus, dm);
+    const u32 up = __shfl_up_sync(FULL, O[3], 1);
+    const u32 below = lane_id() == 0 ? c.dtop : up;
+    u32 O2[4];
+    O2[0] = fshl(below, O[0], 1);
+#pragma unroll
+    for (int j = 1; j < 4; ++j) O2[j] = fshl(O[j - 1], O[j], 1);
+    c.dtop = __shfl_sync(FULL, O[3], 31);
+    if (sign > 0) warp_sub_seg<4>(dp, O2, c.minus, dm);
+    else warp_sub_seg<4>(O2, dp, c.minus, dm);
 }
 
 // Padded shared-memory index: one spare word per 32 makes the lane pattern
@@ -195,11 +205,11 @@ eval_warp_kernel(const u32* __restrict__ in, long in_stride, LevelGeom g, u32* _
     const int W = ((g.n - 1) * g.n >> 5) + 1;
     // staged layout: block i occupies padded slots [i (b + W), i (b + W) + b + W), first W zero
     const int bw = g.b + W;
-    for (int x = lane; x < g.B * bw; x += 32) {
-        const int i = x / bw, xi = x - i * bw - W;
-        const int gi = i * g.b + xi;
-        rs[pad32(x)] = (xi >= 0 && gi < g.s) ? __ldg(row + gi) : 0u;
-    }
+    for (int i = 0; i < g.B; ++i)
+        for (int xo = lane; xo < bw; xo += 32) {
+            const int xi = xo - W, gi = i * g.b + xi;
+            rs[pad32(i * bw + xo)] = (xi >= 0 && gi < g.s) ? __ldg(row + gi) : 0u;
+        }
     __syncwarp();
     auto U = [&](int i, int x) -> u32 {  // limb x of block i (zero outside [0, b))
         return (x < g.b) ? rs[pad32(i * bw + W + x)] : 0u;
