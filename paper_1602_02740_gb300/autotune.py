@@ -22,10 +22,12 @@ import time
 BS = (2, 3, 4, 5, 6, 8, 12, 16, 32)
 LEAF_MIN, LEAF_MAX = 24, 224
 
-# cost-model rates (per second), rough figures measured on GB300
-LEAF_RATE = 4.5e12        # base-case limb products
-INTERP_RATE = 1.5e11      # n^2 x interpolation-value limbs
-EVAL_RATE = 4.0e11        # B x n x evaluation limbs
+# cost-model rates (per second), rough figures measured on GB300 with the current
+# kernels (2^20-bit batch: base case 5.5 T limb products/s; interpolation
+# 2.3-2.9e11 n^2 Y products-limbs/s; evaluation 4-11e11 B n e rows-limbs/s)
+LEAF_RATE = 5.5e12        # base-case limb products
+INTERP_RATE = 2.7e11      # n^2 x interpolation-value limbs
+EVAL_RATE = 6.0e11        # B x n x evaluation limbs
 LAUNCH_S = 6e-6           # per kernel launch
 
 
