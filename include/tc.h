@@ -117,6 +117,35 @@ tc_status tc_mul_batch(tc_ctx *ctx, size_t count,
                        const tc_opts *opts, void *stream);
 
 /*
+ * Prepared batches (the scheduler's work lists; CUDA-graph replay).  The
+ * paper runs the top-level products of one multiplication in parallel
+ * threads (Section 2, eq. 2.5); here any list of products is batched level by
+ * level.  tc_batch_prepare does the host side of tc_mul_batch once for a
+ * fixed list: it groups the products into size classes (padded balanced
+ * lengths), picks each class's plan (`opts` as in tc_mul_batch), uploads the
+ * index tables and allocates the scratch of the largest class -- device memory
+ * owned by the batch, at most the context's budget (else TC_ENOMEM).  Offsets
+ * and lengths are host int64 arrays read during the call only.
+ * tc_batch_run then enqueues kernels and memsets on `stream` and nothing else
+ * (no allocation, no host memory, no synchronisation), so it may be captured
+ * into a CUDA graph and replayed; A, Bv and OUT are device buffers addressed by
+ * the prepared offsets (products of length 0 get zero-filled outputs).  Runs of
+ * one batch must not overlap in time: they share its scratch.
+ * tc_batch_check waits for `stream` and returns TC_ETIMEOUT if a bounded wait
+ * of a segment-parallel level gave up in the last run, else TC_OK.
+ * tc_batch_destroy frees the batch (NULL is ignored).
+ */
+typedef struct tc_batch tc_batch;
+tc_status tc_batch_prepare(tc_ctx *ctx, size_t count, const int64_t *a_off, const int64_t *a_len,
+                           const int64_t *b_off, const int64_t *b_len, const int64_t *out_off,
+                           const tc_opts *opts, tc_batch **out);
+tc_status tc_batch_run(tc_ctx *ctx, const tc_batch *batch, const uint32_t *A, const uint32_t *Bv,
+                       uint32_t *OUT, void *stream);
+tc_status tc_batch_check(tc_ctx *ctx, const tc_batch *batch, void *stream);
+size_t tc_batch_scratch_bytes(const tc_batch *batch);
+void tc_batch_destroy(tc_batch *batch);
+
+/*
  * Uniform batch: `count` balanced products of `limbs` x `limbs` limbs stored
  * as rows.  A row k is A[k * lda .. k * lda + limbs), likewise B; the result
  * row is OUT[k * ldo .. k * ldo + 2 limbs).  Device pointers.

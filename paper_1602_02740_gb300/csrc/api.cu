@@ -1,5 +1,6 @@
 // C-ABI entry points (include/tc.h): context, plans, scratch, level schedule.
 #include <algorithm>
+#include <memory>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -531,6 +532,177 @@ extern "C" tc_status tc_mul_batch(tc_ctx* ctx, size_t count, const uint32_t* A, 
     CK(cudaSetDevice(ctx->device));
     return mul_general(ctx, count, A, a_off, a_len, Bv, b_off, b_len, OUT, out_off, opts,
                        (cudaStream_t)stream);
+}
+
+// ---------------------------------------------------------------------------
+// Prepared batches: the host work of tc_mul_batch (grouping into size
+// classes, index tables, scratch) done once, so that running the batch is
+// kernel launches and memsets only, with no host synchronisation: it can be
+// captured into a CUDA graph and replayed.
+// ---------------------------------------------------------------------------
+struct tc_batch {
+    int device = 0;
+    struct Class {
+        size_t s = 0, cnt = 0;
+        BatchLayout L;
+        size_t tab = 0;  // first entry of this class in each index table
+    };
+    std::vector<Class> classes;
+    std::vector<std::pair<int64_t, int64_t>> zeros;  // (out offset, limbs) of empty products
+    int64_t* tables = nullptr;  // device: aoff, alen, boff, blen, ooff, olen (each `total` long)
+    size_t total = 0;
+    char* scratch = nullptr;    // device: max over classes of level scratch + rows + outputs
+    size_t scratch_bytes = 0;
+};
+
+static size_t class_extra(size_t cnt, size_t s) {
+    return 2 * align256(cnt * s * 4) + align256(cnt * 2 * s * 4);
+}
+
+extern "C" tc_status tc_batch_prepare(tc_ctx* ctx, size_t count, const int64_t* a_off,
+                                      const int64_t* a_len, const int64_t* b_off,
+                                      const int64_t* b_len, const int64_t* out_off,
+                                      const tc_opts* opts, tc_batch** out) {
+    if (!ctx || !out || (count && (!a_off || !a_len || !b_off || !b_len || !out_off))) return TC_EINVAL;
+    *out = nullptr;
+    CK(cudaSetDevice(ctx->device));
+    std::unique_ptr<tc_batch> bt(new tc_batch);
+    bt->device = ctx->device;
+    struct Item { size_t k, cls; };
+    std::vector<Item> items;
+    for (size_t k = 0; k < count; ++k) {
+        if (a_len[k] < 0 || b_len[k] < 0 || a_off[k] < 0 || b_off[k] < 0 || out_off[k] < 0)
+            return TC_EINVAL;
+        if (a_len[k] == 0 || b_len[k] == 0) {
+            if (a_len[k] + b_len[k]) bt->zeros.push_back({out_off[k], a_len[k] + b_len[k]});
+            continue;
+        }
+        items.push_back({k, size_class((size_t)std::max(a_len[k], b_len[k]))});
+    }
+    std::sort(items.begin(), items.end(), [](const Item& x, const Item& y) { return x.cls < y.cls; });
+    std::vector<int64_t> h(6 * items.size());
+    const size_t N = items.size();
+    size_t need = 0;
+    for (size_t i = 0; i < N;) {
+        size_t j = i;
+        while (j < N && items[j].cls == items[i].cls) ++j;
+        tc_batch::Class c;
+        c.s = items[i].cls;
+        c.cnt = j - i;
+        c.tab = i;
+        const tc_opts o = (opts && plan_valid(*opts, c.s)) ? *opts : plan_for(ctx, c.s);
+        c.L = layout_for(c.cnt, c.s, o, false);
+        need = std::max(need, c.L.total + class_extra(c.cnt, c.s));
+        for (size_t t = i; t < j; ++t) {
+            const size_t k = items[t].k;
+            h[t] = a_off[k];
+            h[N + t] = a_len[k];
+            h[2 * N + t] = b_off[k];
+            h[3 * N + t] = b_len[k];
+            h[4 * N + t] = out_off[k];
+            h[5 * N + t] = a_len[k] + b_len[k];
+        }
+        bt->classes.push_back(c);
+        i = j;
+    }
+    if (need > ctx->budget) return TC_ENOMEM;
+    bt->total = N;
+    if (N) {
+        if (cudaMalloc(&bt->tables, h.size() * 8) != cudaSuccess) { cudaGetLastError(); return TC_ENOMEM; }
+        if (cudaMalloc(&bt->scratch, need) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(bt->tables);
+            return TC_ENOMEM;
+        }
+        bt->scratch_bytes = need;
+        const cudaError_t e = cudaMemcpy(bt->tables, h.data(), h.size() * 8, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            cudaFree(bt->tables);
+            cudaFree(bt->scratch);
+            return tc_fail_cuda(e);
+        }
+    }
+    *out = bt.release();
+    return TC_OK;
+}
+
+extern "C" tc_status tc_batch_run(tc_ctx* ctx, const tc_batch* bt, const uint32_t* A,
+                                  const uint32_t* Bv, uint32_t* OUT, void* stream) {
+    if (!ctx || !bt || bt->device != ctx->device) return TC_EINVAL;
+    if (bt->total && (!A || !Bv || !OUT)) return TC_EINVAL;
+    if (!bt->total && !bt->zeros.empty() && !OUT) return TC_EINVAL;
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    for (const auto& z : bt->zeros) CK(cudaMemsetAsync(OUT + z.first, 0, (size_t)z.second * 4, st));
+    const size_t N = bt->total;
+    for (const auto& c : bt->classes) {
+        char* base = bt->scratch;
+        u32* rA = (u32*)(base + c.L.total);
+        u32* rB = (u32*)((char*)rA + align256(c.cnt * c.s * 4));
+        u32* rO = (u32*)((char*)rB + align256(c.cnt * c.s * 4));
+        const int64_t* aoff = bt->tables + c.tab;
+        const int64_t* alen = bt->tables + N + c.tab;
+        const int64_t* boff = bt->tables + 2 * N + c.tab;
+        const int64_t* blen = bt->tables + 3 * N + c.tab;
+        const int64_t* ooff = bt->tables + 4 * N + c.tab;
+        const int64_t* olen = bt->tables + 5 * N + c.tab;
+        for (size_t c0 = 0; c0 < c.cnt; c0 += 65535) {
+            const int cc = (int)std::min<size_t>(65535, c.cnt - c0);
+            dim3 grid((unsigned)std::min<size_t>((c.s + 255) / 256, 64), cc);
+            gather_rows<<<grid, 256, 0, st>>>(A, aoff + c0, alen + c0, (int)c.s, rA + c0 * c.s, cc);
+            gather_rows<<<grid, 256, 0, st>>>(Bv, boff + c0, blen + c0, (int)c.s, rB + c0 * c.s, cc);
+        }
+        CK(cudaGetLastError());
+        // no context: no phase events and no host read-back inside a possibly captured run
+        tc_status e = run_uniform(c.L, base, c.cnt, c.s, rA, (long)c.s, rB, (long)c.s, rO,
+                                  (long)(2 * c.s), false, st, nullptr);
+        if (e) return e;
+        for (size_t c0 = 0; c0 < c.cnt; c0 += 65535) {
+            const int cc = (int)std::min<size_t>(65535, c.cnt - c0);
+            dim3 grid((unsigned)std::min<size_t>((2 * c.s + 255) / 256, 64), cc);
+            scatter_rows<<<grid, 256, 0, st>>>(rO + c0 * 2 * c.s, (int)(2 * c.s), ooff + c0,
+                                               olen + c0, OUT, cc);
+        }
+        CK(cudaGetLastError());
+    }
+    return TC_OK;
+}
+
+extern "C" size_t tc_batch_scratch_bytes(const tc_batch* bt) { return bt ? bt->scratch_bytes : 0; }
+
+// After a run (direct or replayed) has completed on `stream`: TC_ETIMEOUT if a
+// bounded wait of a segment-parallel level gave up, else TC_OK.  Synchronises.
+extern "C" tc_status tc_batch_check(tc_ctx* ctx, const tc_batch* bt, void* stream) {
+    if (!ctx || !bt || bt->device != ctx->device) return TC_EINVAL;
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    for (const auto& c : bt->classes) {
+        for (size_t l = 0; l < c.L.g.size(); ++l) {
+            int* words[2] = {nullptr, nullptr};
+            if (use_wide(c.L.g[l], c.L.P[l])) words[0] = wide_error_word(bt->scratch + c.L.work[l], c.L.g[l], c.L.P[l]);
+            if (use_wide_eval(c.L.g[l], c.L.P[l]))
+                words[1] = wide_eval_error_word(bt->scratch + c.L.evwork[l], c.L.g[l], c.L.P[l]);
+            for (int* w : words) {
+                if (!w) continue;
+                int flag = 0;
+                CK(cudaMemcpyAsync(&flag, w, sizeof(int), cudaMemcpyDeviceToHost, st));
+                CK(cudaStreamSynchronize(st));
+                if (flag) return TC_ETIMEOUT;
+            }
+        }
+    }
+    return TC_OK;
+}
+
+extern "C" void tc_batch_destroy(tc_batch* bt) {
+    if (!bt) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(bt->device);
+    if (bt->tables) cudaFree(bt->tables);
+    if (bt->scratch) cudaFree(bt->scratch);
+    cudaSetDevice(cur);
+    delete bt;
 }
 
 extern "C" tc_status tc_mul(tc_ctx* ctx, const uint32_t* a, size_t na, const uint32_t* b, size_t nb,

@@ -61,6 +61,12 @@ _SIGS = {
     "tc_sqr": (ctypes.c_int, [_vp, _u32p, _sz, _u32p, _optp, _vp]),
     "tc_mul_batch": (ctypes.c_int, [_vp, _sz, _u32p, _i64p, _i64p, _u32p, _i64p, _i64p, _u32p,
                                     _i64p, _optp, _vp]),
+    "tc_batch_prepare": (ctypes.c_int, [_vp, _sz, _i64p, _i64p, _i64p, _i64p, _i64p, _optp,
+                                        ctypes.POINTER(ctypes.c_void_p)]),
+    "tc_batch_run": (ctypes.c_int, [_vp, _vp, _u32p, _u32p, _u32p, _vp]),
+    "tc_batch_check": (ctypes.c_int, [_vp, _vp, _vp]),
+    "tc_batch_scratch_bytes": (ctypes.c_size_t, [_vp]),
+    "tc_batch_destroy": (None, [_vp]),
     "tc_mul_uniform": (ctypes.c_int, [_vp, _sz, _sz, _u32p, _sz, _u32p, _sz, _u32p, _sz, _optp, _vp]),
     "tc_mul_uniform_host": (ctypes.c_int, [_vp, _sz, _sz, _u32p, _u32p, _u32p, _optp, _vp]),
     "tc_schoolbook": (ctypes.c_int, [_sz, _sz, _u32p, _sz, _u32p, _sz, _u32p, _sz, _vp]),
@@ -237,6 +243,52 @@ def tc_mul_batch(ctx: Context, A, a_off, a_len, B, b_off, b_len, OUT, out_off, p
                               _ptr(B), arrs[2].ctypes.data, arrs[3].ctypes.data, _ptr(OUT),
                               arrs[4].ctypes.data, _opts(plan), _stream(stream)), "tc_mul_batch")
     return OUT
+
+
+class Batch:
+    """A prepared batch (tc_batch_prepare); frees its device tables and scratch on close()."""
+
+    def __init__(self, handle):
+        self.handle = handle
+
+    def close(self):
+        if self.handle:
+            lib().tc_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def tc_batch_prepare(ctx: Context, a_off, a_len, b_off, b_len, out_off, plan=None) -> Batch:
+    """Host-side preparation of a packed batch (offsets/lengths: host int64 arrays)."""
+    arrs = [np.ascontiguousarray(x, dtype=np.int64) for x in (a_off, a_len, b_off, b_len, out_off)]
+    h = ctypes.c_void_p()
+    _check(lib().tc_batch_prepare(ctx.handle, len(arrs[0]), *(x.ctypes.data for x in arrs),
+                                  _opts(plan), ctypes.byref(h)), "tc_batch_prepare")
+    return Batch(h.value)
+
+
+def tc_batch_run(ctx: Context, batch: Batch, A, B, OUT, stream=None):
+    """Enqueue the prepared batch on `stream` (kernels and memsets only: capturable)."""
+    _check(lib().tc_batch_run(ctx.handle, batch.handle, _ptr(A), _ptr(B), _ptr(OUT),
+                              _stream(stream)), "tc_batch_run")
+    return OUT
+
+
+def tc_batch_check(ctx: Context, batch: Batch, stream=None):
+    _check(lib().tc_batch_check(ctx.handle, batch.handle, _stream(stream)), "tc_batch_check")
+
+
+def tc_batch_scratch_bytes(batch: Batch) -> int:
+    return lib().tc_batch_scratch_bytes(batch.handle)
+
+
+def tc_batch_destroy(batch: Batch):
+    batch.close()
 
 
 def tc_schoolbook(A, B, OUT=None, stream=None):

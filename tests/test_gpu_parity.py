@@ -220,6 +220,59 @@ def test_batch_mixed_sizes(ctx, tc):
     assert np.array_equal(host(OUT), want)
 
 
+def _packed(la, lb, seed):
+    a_off = np.concatenate([[0], np.cumsum(la)[:-1]])
+    b_off = np.concatenate([[0], np.cumsum(lb)[:-1]])
+    o_off = np.concatenate([[0], np.cumsum(la + lb)[:-1]])
+    A = inputs.uniform(max(1, int(la.sum())), seed)
+    B = inputs.uniform(max(1, int(lb.sum())), seed + 1)
+    return A, B, a_off, b_off, o_off
+
+
+def test_prepared_batch_run_and_graph_replay(ctx, tc):
+    """A prepared batch gives the products directly and when its run is captured
+    into a CUDA graph and replayed; zero-length products get zero outputs."""
+    import torch
+    t = tc.tc
+    la, lb = inputs.batch_lengths(150, seed=9, lo=64, hi=9000)
+    la[3], lb[7] = 0, 0
+    A, B, a_off, b_off, o_off = _packed(la, lb, 40)
+    n_out = int((la + lb).sum())
+    want = native.schoolbook_batch(A, a_off, la, B, b_off, lb, o_off, n_out)
+    dA, dB = dev(A), dev(B)
+    bt = t.tc_batch_prepare(ctx, a_off, la, b_off, lb, o_off)
+    assert t.tc_batch_scratch_bytes(bt) > 0
+    OUT = torch.full((n_out,), -1, dtype=torch.int32, device="cuda")
+    t.tc_batch_run(ctx, bt, dA, dB, OUT)
+    t.tc_batch_check(ctx, bt)
+    assert np.array_equal(host(OUT), want)
+    # capture one run and replay it into a fresh output
+    OUT2 = torch.full((n_out,), -1, dtype=torch.int32, device="cuda")
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        t.tc_batch_run(ctx, bt, dA, dB, OUT2, stream=s)
+    OUT2.fill_(-1)
+    graph.replay()
+    torch.cuda.synchronize()
+    assert np.array_equal(host(OUT2), want)
+    # replay on new operand values in the same buffers
+    A2 = inputs.uniform(A.size, 77)
+    dA.copy_(dev(A2))
+    graph.replay()
+    torch.cuda.synchronize()
+    want2 = native.schoolbook_batch(A2, a_off, la, B, b_off, lb, o_off, n_out)
+    assert np.array_equal(host(OUT2), want2)
+    bt.close()
+
+
+def test_prepared_batch_rejects_bad_input(ctx, tc):
+    t = tc.tc
+    with pytest.raises(t.TCError):
+        t.tc_batch_prepare(ctx, [0], [-1], [0], [4], [0])
+
+
 # ---------------------------------------------------------------- base case, large batches
 # 4096 or more products select the lane-per-product kernels: a lane pair per
 # product (rows in shared memory) up to 792 limbs, one lane per product from
