@@ -62,6 +62,10 @@ def parse():
                    help="products in the mixed-size batch measurement (0 = skip)")
     p.add_argument("--serve", type=int, default=2000,
                    help="requests per serving run (the full serving workload is 20000; 0 = skip)")
+    p.add_argument("--no-configs", action="store_true",
+                   help="skip the Toom-3 at 1024 limbs and the all-ones / sparse 2^20-bit lines")
+    p.add_argument("--large", action="store_true",
+                   help="also time single products of 2^24, 2^26 and 2^27 bits (and squares)")
     return p.parse_args()
 
 
@@ -420,6 +424,58 @@ def main():
                 sweep[str(Btop)] = {"plan": best[1], "mults_per_s": P / (best[0] / 1e3),
                                     "ns_per_product": best[0] * 1e6 / P}
 
+    # ---- the other configurations: Toom-3 at 1024 limbs; all-ones and sparse limbs ----
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    configs = None
+    if not args.no_configs:
+        configs = {}
+        # one Toom-3 level over a batch of 1024-limb products, and one product alone
+        n3 = 16384
+        a3 = torch.randint(-2 ** 31, 2 ** 31 - 1, (n3, 1024), dtype=torch.int32, device="cuda")
+        b3 = torch.randint(-2 ** 31, 2 ** 31 - 1, (n3, 1024), dtype=torch.int32, device="cuda")
+        o3 = torch.empty((n3, 2048), dtype=torch.int32, device="cuda")
+
+        ms_b = timed(lambda: tc.tc_mul_uniform(ctx, a3, b3, o3, plan=[3]), 10)
+        ms_1 = timed(lambda: tc.tc_mul(ctx, a3[0], b3[0], o3[0], plan=[3]), 1000)
+        configs["toom3_1024_limbs"] = {"plan": [3], "batch": n3,
+                                       "ns_per_product_batched": ms_b * 1e6 / n3,
+                                       "ns_per_product_single": ms_1 * 1e6, "reps_single": 1000}
+        del a3, b3, o3
+        # the headline batch with all-ones and with sparse limbs (1 % nonzero)
+        from paper_1602_02740_gb300 import inputs as _inputs
+        for kind in ("all_ones", "sparse"):
+            rows = np.stack([_inputs.operand(kind, L, 500 + k) for k in range(8)])
+            reps_rows = np.tile(rows, (P // 8 + 1, 1))[:P]
+            dA2 = torch.from_numpy(reps_rows.view(np.int32)).to("cuda")
+            ms_k = timed(lambda: tc.tc_mul_uniform(ctx, dA2, dA2 if kind == "all_ones" else dB, dO,
+                                                   plan=used_plan), 3)
+            configs[f"{kind}_2e20"] = {"mults_per_s": P / (ms_k / 1e3), "plan": used_plan,
+                                       "operands": "all-ones squared" if kind == "all_ones"
+                                       else "sparse (1 % nonzero limbs) x uniform"}
+            del dA2
+    large = None
+    if args.large:
+        large = {}
+        for Lg in (1 << 19, 1 << 21, 1 << 22):
+            ga = torch.randint(-2 ** 31, 2 ** 31 - 1, (Lg,), dtype=torch.int32, device="cuda")
+            gb = torch.randint(-2 ** 31, 2 ** 31 - 1, (Lg,), dtype=torch.int32, device="cuda")
+            go = torch.empty(2 * Lg, dtype=torch.int32, device="cuda")
+            ms_m = timed(lambda: tc.tc_mul(ctx, ga, gb, go), 3)
+            ms_s = timed(lambda: tc.tc_sqr(ctx, ga, go), 3)
+            large[f"2^{(Lg * 32).bit_length() - 1}_bits"] = {
+                "plan": tc.tc_plan_for(ctx, Lg), "ms_mul": ms_m, "ms_sqr": ms_s}
+            del ga, gb, go
+
     mixed = mixed_batch(ctx, tc, args.mixed, rank) if args.mixed else None
     serve = serving(ctx, tc, args.serve, rank) if args.serve else None
 
@@ -474,7 +530,7 @@ def main():
                        "limbs": L, "batch_per_gpu": P, "plan": used_plan,
                        "l2": f"operands ({2 * P * L * 4 / 1e6:.0f} MB) exceed the 129 MB L2; no flush"},
             "roofline": roof, "phases": phase_summary, "sweep": sweep,
-            "mixed_batch": mixed, "serving": serve,
+            "mixed_batch": mixed, "serving": serve, "configs": configs, "large": large,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
         }
         print(json.dumps(line), flush=True)
