@@ -4,7 +4,8 @@ and 32 with recursive Toom-Cook below, and squaring at the same sizes.
 At these sizes the oracle checks properties that hold at any size: the
 product modulo three 61-bit primes, and the exact low 4096 limbs, which only
 depend on the low 4096 limbs of each operand (computed by the oracle's own
-product of those parts)."""
+product of those parts).  One 2^24-bit product and one square are also
+compared limb by limb with CPython's integer product (about 10 s each)."""
 import numpy as np
 import pytest
 
@@ -88,3 +89,16 @@ def test_wide_evaluation_sign_edges(ctx, tc, kind, plan):
         b = inputs.sparse(L, 23)
     out = t.to_numpy(t.tc_mul(ctx, t.to_device(a), t.to_device(b), plan=plan))
     assert np.array_equal(out, from_int(to_int(a) * to_int(b), 2 * L))
+
+
+@pytest.mark.parametrize("square", [False, True])
+def test_large_product_exact_2e24(ctx, tc, square):
+    """Every limb of a 2^24-bit product (the plan table's plan) against CPython."""
+    t = tc.tc
+    L = 1 << 19
+    a = inputs.uniform(L, 91)
+    b = a if square else inputs.uniform(L, 92)
+    da = t.to_device(a)
+    out = t.to_numpy(t.tc_sqr(ctx, da) if square else t.tc_mul(ctx, da, t.to_device(b)))
+    want = from_int(to_int(a) * to_int(b), 2 * L)
+    assert np.array_equal(out, want)
