@@ -194,6 +194,8 @@ struct DivConst {
     u32 inv;     // d^-1 mod 2^32
     u32 ninv;    // -d^-1 mod 2^32
     u32 rkm[5];  // (rho^KL)^(2^i) 2^32 mod d: Montgomery form of the scan multipliers
+    u32 unit;    // 1 when rho^KL = 1 (mod d) and d < 2^26: the scan is a plain sum
+    u32 recip;   // floor((2^32 - 1) / d), for reductions of small sums mod d
 };
 
 // Montgomery product a b 2^-32 mod d for a, b < d < 2^31.
@@ -363,6 +365,14 @@ __device__ __forceinline__ void warp_sub_seg(const u32 a[KL], const u32 b[KL], u
 }
 
 // Exact division of a warp chunk of 32 KL limbs by dc.d (constants built for this KL).
+// x mod d for x < 2^32, d odd (q below is floor(x / d) or at most two less).
+__device__ __forceinline__ u32 mod_small(u32 x, u32 d, u32 recip) {
+    const u32 q = __umulhi(x, recip);
+    u32 r = x - q * d;
+    r = r >= d ? r - d : r;
+    return r >= d ? r - d : r;
+}
+
 template <int KL>
 __device__ __forceinline__ void warp_exact_div_seg(u32 v[KL], const DivConst& dc, u32& borrow) {
     const int lane = lane_id();
@@ -370,6 +380,29 @@ __device__ __forceinline__ void warp_exact_div_seg(u32 v[KL], const DivConst& dc
     u32 b0 = 0;
 #pragma unroll
     for (int j = 0; j < KL; ++j) b0 = div_step(v[j], b0, dc.d, dc.inv, q);
+    if (dc.unit) {
+        // rho^KL = 1 (e.g. d = 2^m - 1 with m | 32 KL): a lane's borrow out is its own
+        // b0 plus its borrow in, mod d, so the borrows are prefix sums (each b0 <= d,
+        // so 32 of them plus the chunk's borrow stay below 2^32 for d < 2^26)
+        u32 s = b0 + (lane == 0 ? borrow : 0u);
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+            const int w = 1 << i;
+            const u32 o = __shfl_up_sync(FULL, s, w);
+            if (lane >= w) s += o;
+        }
+        s = mod_small(s, dc.d, dc.recip);
+        u32 bin = __shfl_up_sync(FULL, s, 1);
+        if (lane == 0) bin = borrow;
+        u32 B = bin;
+#pragma unroll
+        for (int j = 0; j < KL; ++j) {
+            B = div_step(v[j], B, dc.d, dc.inv, q);
+            v[j] = q;
+        }
+        borrow = __shfl_sync(FULL, s, 31);
+        return;
+    }
     u32 t = b0;
     if (lane == 0) {
         const u32 x = mont_mul(borrow, dc.rkm[0], dc.d, dc.ninv) + t;

@@ -372,6 +372,8 @@ static DivConst make_div(u32 d, int KL) {
     c.inv = inv32(d);
     c.ninv = 0u - c.inv;
     for (int i = 0; i < 5; ++i) c.rkm[i] = 0;
+    c.unit = (d > 1 && d < (1u << 26) && powmod_host(2, 32ull * KL, d) == 1) ? 1u : 0u;
+    c.recip = d > 1 ? 0xffffffffu / d : 0u;
     if (d > 1) {
         // rk = rho^KL = 2^(-32 KL) mod d: the inverse of 2^(32 KL) mod d by extended Euclid.
         const u32 t = powmod_host(2, 32ull * KL, d);
