@@ -1357,36 +1357,42 @@ interp_reg_kernel(InterpArgs a, DivTable dt, long P) {
         }
     }
     // ---- recompose out[l] = sum_t w_t[l - t b] from shared memory ----
-    u32* sw = sm + (long)warp * 2 * (N + 1) * C;
+    // Term t (w_2i = ce_i, w_2i+1 = co_(i+1)) is stored shifted by d_t = (t b) mod 4
+    // words inside a slot of C + 4 words, so limb l - t b of it sits at a 16-byte
+    // aligned index whenever l is a multiple of 4: one vector load per term per lane.
+    constexpr int SLOT = C + 4;
+    u32* sw = sm + (long)warp * (2 * N + 1) * SLOT;
+    const int b = g.b;
 #pragma unroll
-    for (int p = 0; p < 2; ++p)
+    for (int t = 0; t <= 2 * N; ++t) {
+        const u32* w = c[t & 1][(t + 1) >> 1];
+        u32* slot = sw + t * SLOT;
+        const int dt = (t * b) & 3;
+        if (lane == 0) { slot[0] = slot[1] = slot[2] = slot[3] = 0u; }
+        if (lane == 31) { slot[C] = slot[C + 1] = slot[C + 2] = slot[C + 3] = 0u; }
+        __syncwarp();
 #pragma unroll
-        for (int m = 0; m <= N; ++m) st_seg<KL>(sw + (p * (N + 1) + m) * C + KL * lane, c[p][m]);
+        for (int j = 0; j < KL; ++j) slot[dt + KL * lane + j] = w[j];
+    }
     __syncwarp();
     u32* out = a.out + k * a.out_stride;
     const bool aligned = ((reinterpret_cast<uintptr_t>(out) & 15u) == 0);
     UnsignedNorm nst{0, 0};
-    const int nterms = 2 * N + 1;
     for (int base_l = 0; base_l < a.out_len; base_l += CH) {
-        u64 cols[4];
+        u64 cols[4] = {0, 0, 0, 0};
         const int l0 = base_l + 4 * lane;
-        const int t0 = l0 / g.b;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int l = l0 + j;
-            u64 S = 0;
-            if (l < a.out_len) {
-                int t = t0;
-                while ((t + 1) * g.b <= l) ++t;  // t = floor(l / b)
-                if (t > nterms - 1) t = nterms - 1;
-                for (; t >= 0; --t) {
-                    const int x = l - t * g.b;
-                    if (x >= C) break;
-                    S += sw[((t & 1) * (N + 1) + ((t + 1) >> 1)) * C + x];
-                }
-            }
-            cols[j] = S;
+        for (int t = 0; t <= 2 * N; ++t) {
+            if (base_l + CH <= t * b || base_l >= t * b + C) continue;  // warp-uniform
+            const int dt = (t * b) & 3;
+            const int x = l0 - t * b;  // x + dt is a multiple of 4
+            if (x < -dt || x > C - dt) continue;
+            const uint4 q = *reinterpret_cast<const uint4*>(sw + t * SLOT + dt + x);
+            cols[0] += q.x; cols[1] += q.y; cols[2] += q.z; cols[3] += q.w;
         }
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (l0 + j >= a.out_len) cols[j] = 0;
         u32 d[4];
         warp_norm_unsigned(cols, nst, d);
         if (aligned && l0 + 4 <= a.out_len) {
@@ -1411,7 +1417,7 @@ static int reg_interp_kl(const LevelGeom& g) {
 template <int KL, int N>
 static cudaError_t launch_reg_interp(const InterpArgs& a, long P, cudaStream_t st) {
     static const DivTable dtk = make_div_table(KL);
-    const size_t per_warp = (size_t)2 * (N + 1) * 32 * KL * 4;
+    const size_t per_warp = (size_t)(2 * N + 1) * (32 * KL + 4) * 4;
     int wpb = (int)((96 * 1024) / per_warp);
     if (wpb > 8) wpb = 8;
     if (wpb < 1) wpb = 1;
