@@ -192,6 +192,131 @@ eval_kernel(const u32* __restrict__ in, long in_stride, LevelGeom g, u32* __rest
 
 // Short rows: one warp per row, every point of the row, the row staged in
 // shared memory (padded layout), several rows per block, no block barriers.
+// Warp per row for small B (B <= 8, every shift j i < 64 bits): the same staging
+// as eval_warp_kernel, but each 128-limb chunk's block limbs are read once and
+// serve all points x = 2^j (column sums for every j from the same registers),
+// and the top-down sign scans of all points share their loads.
+template <int BB>
+__global__ void __launch_bounds__(256)
+eval_pts_kernel(const u32* __restrict__ in, long in_stride, LevelGeom g, u32* __restrict__ out,
+                uint8_t* __restrict__ sgn, long P, int rowlen) {
+    constexpr int N = BB - 1;
+    extern __shared__ __align__(16) u32 rows_sm[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long k = (long)blockIdx.x * (blockDim.x >> 5) + warp;
+    if (k >= P) return;  // warp-uniform
+    u32* rs = rows_sm + (long)warp * rowlen;
+    const u32* row = in + k * in_stride;
+    const int npts = 2 * BB - 1;
+    const int W = ((N - 1) * N >> 5) + 1;
+    const int bw = g.b + W;
+    for (int i = 0; i < BB; ++i)
+        for (int xo = lane; xo < bw; xo += 32) {
+            const int xi = xo - W, gi = i * g.b + xi;
+            rs[pad32(i * bw + xo)] = (xi >= 0 && gi < g.s) ? __ldg(row + gi) : 0u;
+        }
+    __syncwarp();
+    auto U = [&](int i, int x) -> u32 {  // limb x of block i (zero outside [0, b))
+        return (x >= 0 && x < g.b) ? rs[pad32(i * bw + W + x)] : 0u;
+    };
+    u32* orow0 = out + (k * npts) * (long)g.estride;
+    for (int pos = 4 * lane; pos < g.estride; pos += CH) {
+        u32 v[4];
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) v[jj] = (pos + jj < g.s) ? U(0, pos + jj) : 0u;
+        st4(orow0 + pos, v);
+    }
+    // ---- signs of E - O at every x = 2^j, top-down, loads shared ----
+    i64 T[N];
+    int sign[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) { T[j] = 0; sign[j] = 0; }
+    for (int top = g.e - 1; top >= 0; top -= 32) {
+        bool open = false;
+#pragma unroll
+        for (int j = 0; j < N; ++j) open |= sign[j] == 0;
+        if (!open) break;
+        const int l = top - lane;
+        u32 w[BB][3];  // limbs l-2, l-1, l of each block
+#pragma unroll
+        for (int i = 0; i < BB; ++i) {
+            w[i][0] = l >= 0 ? U(i, l - 2) : 0u;
+            w[i][1] = l >= 0 ? U(i, l - 1) : 0u;
+            w[i][2] = l >= 0 ? U(i, l) : 0u;
+        }
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            if (sign[j] != 0) continue;
+            i64 d = 0;
+            if (l >= 0) {
+                u64 e = 0, o = 0;
+#pragma unroll
+                for (int i = 0; i < BB; ++i) {
+                    const int sh = j * i, qa = sh >> 5, r = sh & 31;
+                    const u32 tv = fshl(w[i][1 - qa], w[i][2 - qa], (u32)r);
+                    if (i & 1) o += tv; else e += tv;
+                }
+                d = (i64)e - (i64)o;
+            }
+            const unsigned nz = __ballot_sync(FULL, d != 0);
+            if (T[j] == 0 && nz == 0) continue;
+            for (int tt = 0; tt < 32; ++tt) {
+                const i64 dt = __shfl_sync(FULL, d, tt);
+                if (top - tt < 0) break;
+                T[j] = T[j] * 4294967296LL + dt;
+                if (T[j] >= 17) { sign[j] = 1; break; }
+                if (T[j] <= -17) { sign[j] = -1; break; }
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < N; ++j)
+        if (sign[j] == 0) sign[j] = T[j] < 0 ? -1 : 1;
+    // ---- bottom-up: every point of a chunk from one read of the block limbs ----
+    UnsignedNorm ne[N], no[N];
+    EvalCarry cpm[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) { ne[j] = {0, 0}; no[j] = {0, 0}; cpm[j] = {0, 0}; }
+    for (int base = 0; base < g.estride; base += CH) {
+        const int l0 = base + 4 * lane;
+        u32 v[BB][6];  // limbs l0-2 .. l0+3 of each block
+#pragma unroll
+        for (int i = 0; i < BB; ++i)
+#pragma unroll
+            for (int q = 0; q < 6; ++q) v[i][q] = U(i, l0 - 2 + q);
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            u64 e[4] = {0, 0, 0, 0}, o[4] = {0, 0, 0, 0};
+#pragma unroll
+            for (int i = 0; i < BB; ++i) {
+                const int sh = j * i, qa = sh >> 5, r = sh & 31;
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) {
+                    const u32 tv = fshl(v[i][jj - qa + 1], v[i][jj - qa + 2], (u32)r);
+                    if (i & 1) o[jj] += tv; else e[jj] += tv;
+                }
+            }
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj)
+                if (l0 + jj >= g.e) { e[jj] = 0; o[jj] = 0; }
+            u32 dp[4], dm[4];
+            eval_finish(e, o, sign[j], ne[j], no[j], cpm[j], dp, dm);
+            if (l0 < g.estride) {
+                st4(out + (k * npts + 2 * j + 1) * (long)g.estride + l0, dp);
+                st4(out + (k * npts + 2 * j + 2) * (long)g.estride + l0, dm);
+            }
+        }
+    }
+    if (lane == 0) {
+        sgn[k * npts] = 0;
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            sgn[k * npts + 2 * j + 1] = 0;
+            sgn[k * npts + 2 * j + 2] = sign[j] < 0 ? 1 : 0;
+        }
+    }
+}
+
 __global__ void __launch_bounds__(256)
 eval_warp_kernel(const u32* __restrict__ in, long in_stride, LevelGeom g, u32* __restrict__ out,
                  uint8_t* __restrict__ sgn, long P, int rowlen) {
@@ -309,6 +434,16 @@ cudaError_t launch_eval(const u32* in, long in_stride, const LevelGeom& g, u32* 
             if (wpb > 8) wpb = 8;
             if (wpb < 1) wpb = 1;
             const long grid = (P + wpb - 1) / wpb;
+            const size_t smem = (size_t)wpb * rowlen * 4;
+            switch (g.B) {
+#define TC_EVAL_PTS(BB) \
+    case BB: eval_pts_kernel<BB><<<(unsigned)grid, wpb * 32, smem, st>>>(in, in_stride, g, out, sgn, P, rowlen); \
+        return cudaGetLastError();
+                TC_EVAL_PTS(2) TC_EVAL_PTS(3) TC_EVAL_PTS(4) TC_EVAL_PTS(5)
+                TC_EVAL_PTS(6) TC_EVAL_PTS(7) TC_EVAL_PTS(8)
+#undef TC_EVAL_PTS
+                default: break;
+            }
             eval_warp_kernel<<<(unsigned)grid, wpb * 32, (size_t)wpb * rowlen * 4, st>>>(
                 in, in_stride, g, out, sgn, P, rowlen);
             return cudaGetLastError();
@@ -1053,9 +1188,9 @@ interp_stream_kernel(InterpArgs a, DivTable dt, FinTable ft, long P) {
                     u32 x[KL], z[KL] = {0, 0, 0, 0}, dv[KL], e[KL + 2];
                     ldv(V(p, m), x);
                     if (m > 1 || p == 0) ldv(V(p, m - 1), z);
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) mst[p][i] = sm8[4 * p + i];
                     if (f1 > 1) {
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) mst[p][i] = sm8[4 * p + i];
                         u32 zz[KL];
                         warp_mul_small<KL>(z, f1, mst[p][0], mst[p][1], zz);
 #pragma unroll
