@@ -488,6 +488,87 @@ __device__ __forceinline__ void double_add_squares(u32* R, const u32* a) {
         : "r"(S[0]), "r"(S[1]), "r"(S[2]), "r"(S[3]), "r"(S[4]), "r"(S[5]), "r"(S[6]), "r"(S[7]));
 }
 
+// One anti-diagonal of the pair kernel; OFF is the ring offset of the window's
+// column 0 among the twelve accumulator slots (slot (OFF + k) mod 12 holds
+// column 8D + 4h + k).
+template <bool SQ>
+struct PairDiag {
+    const u32* ra;
+    const u32* rb;
+    u32* out;
+    int T, h;
+    bool emit, aligned;
+    int out_len;
+
+    template <int OFF>
+    __device__ __forceinline__ void step(int D, u32 (&lo)[12], u32 (&mid)[12], u32 (&hi)[12],
+                                         u32 (&cin)[3]) const {
+        auto S = [](int k) { return (OFF + k) % 12; };
+        const int Ilo = D - T + 1 > 0 ? D - T + 1 : 0;
+        int Ihi = D < T - 1 ? D : T - 1;
+        if (SQ && Ihi > D / 2) Ihi = D / 2;
+        for (int I = Ilo; I <= Ihi; ++I) {
+            const int J = D - I;
+            const uint4 av = ld4(ra + 8 * I + 4 * h);
+            const uint4 b0 = ld4(rb + 8 * J), b1 = ld4(rb + 8 * J + 4);
+            const u32 a4[4] = {av.x, av.y, av.z, av.w};
+            const u32 b8[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+            if (SQ && I == J) {
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int c = 0; c < 8; ++c)
+                        mac96(lo[S(r + c)], mid[S(r + c)], hi[S(r + c)], a4[r], c > 4 * h + r ? b8[c] : 0u);
+            } else {
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) mac96(lo[S(r + c)], mid[S(r + c)], hi[S(r + c)], a4[r], b8[c]);
+            }
+        }
+        // the odd lane's columns 0..7 join the even lane's columns 4..11
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const u32 pl = __shfl_down_sync(FULL, lo[S(k)], 1);
+            const u32 pm = __shfl_down_sync(FULL, mid[S(k)], 1);
+            const u32 ph = __shfl_down_sync(FULL, hi[S(k)], 1);
+            if (h == 0) add96(lo[S(k + 4)], mid[S(k + 4)], hi[S(k + 4)], pl, pm, ph);
+        }
+        // columns 8D .. 8D+7 (even lane): the limbs of sum_k (lo_k + mid_k 2^32 + hi_k 2^64)
+        // 2^(32k), k < 8, by two carry chains.  What spills past column 8D+7 (three
+        // words) is the next diagonal's carry: added into column 8 (the next window's
+        // column 0), or, when squaring, kept apart because the columns get doubled.
+        const u32 wl[8] = {lo[S(0)], lo[S(1)], lo[S(2)], lo[S(3)], lo[S(4)], lo[S(5)], lo[S(6)], lo[S(7)]};
+        const u32 wm[8] = {mid[S(0)], mid[S(1)], mid[S(2)], mid[S(3)], mid[S(4)], mid[S(5)], mid[S(6)], mid[S(7)]};
+        const u32 wh[8] = {hi[S(0)], hi[S(1)], hi[S(2)], hi[S(3)], hi[S(4)], hi[S(5)], hi[S(6)], hi[S(7)]};
+        u32 R[11];
+        add8_shifted(wl, wm, wh, R);
+        if (SQ) {
+            const uint4 sq = ld4(ra + 4 * D);  // a_(4D + k/2) for the even columns (zeros past s)
+            const u32 sqv[4] = {sq.x, sq.y, sq.z, sq.w};
+            double_add_squares(R, sqv);
+            add3_into11(R, cin[0], cin[1], cin[2]);
+            cin[0] = R[8]; cin[1] = R[9]; cin[2] = R[10];
+        } else if (h == 0) {
+            add96(lo[S(8)], mid[S(8)], hi[S(8)], R[8], R[9], R[10]);
+        }
+        if (emit) {
+            const int c0 = 8 * D;
+            if (aligned && c0 + 8 <= out_len) {
+                st4(out + c0, R);
+                st4(out + c0 + 4, R + 4);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 8; ++k)
+                    if (c0 + k < out_len) out[c0 + k] = R[k];
+            }
+        }
+        // columns 0..7 are done: their slots become columns 4..11 of the next window
+#pragma unroll
+        for (int k = 0; k < 8; ++k) { lo[S(k)] = 0; mid[S(k)] = 0; hi[S(k)] = 0; }
+    }
+};
+
 template <bool SQ>
 __global__ void __launch_bounds__(32 * PAIR_WARPS)
 leaf_pair_kernel(const u32* __restrict__ A, long lda, const u32* __restrict__ Bm, long ldb,
@@ -536,70 +617,18 @@ leaf_pair_kernel(const u32* __restrict__ A, long lda, const u32* __restrict__ Bm
     u32 lo[12], mid[12], hi[12], cin[3] = {0, 0, 0};
 #pragma unroll
     for (int k = 0; k < 12; ++k) { lo[k] = 0; mid[k] = 0; hi[k] = 0; }
-    for (int D = 0; D <= 2 * T - 1; ++D) {
-        const int Ilo = D - T + 1 > 0 ? D - T + 1 : 0;
-        int Ihi = D < T - 1 ? D : T - 1;
-        if (SQ && Ihi > D / 2) Ihi = D / 2;
-        for (int I = Ilo; I <= Ihi; ++I) {
-            const int J = D - I;
-            const uint4 av = ld4(ra + 8 * I + 4 * h);
-            const uint4 b0 = ld4(rb + 8 * J), b1 = ld4(rb + 8 * J + 4);
-            const u32 a4[4] = {av.x, av.y, av.z, av.w};
-            const u32 b8[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-            if (SQ && I == J) {
-#pragma unroll
-                for (int r = 0; r < 4; ++r)
-#pragma unroll
-                    for (int c = 0; c < 8; ++c)
-                        mac96(lo[r + c], mid[r + c], hi[r + c], a4[r], c > 4 * h + r ? b8[c] : 0u);
-            } else {
-#pragma unroll
-                for (int r = 0; r < 4; ++r)
-#pragma unroll
-                    for (int c = 0; c < 8; ++c) mac96(lo[r + c], mid[r + c], hi[r + c], a4[r], b8[c]);
-            }
-        }
-        // the odd lane's slots 0..7 join the even lane's slots 4..11
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const u32 pl = __shfl_down_sync(FULL, lo[k], 1);
-            const u32 pm = __shfl_down_sync(FULL, mid[k], 1);
-            const u32 ph = __shfl_down_sync(FULL, hi[k], 1);
-            if (h == 0) add96(lo[k + 4], mid[k + 4], hi[k + 4], pl, pm, ph);
-        }
-        // columns 8D .. 8D+7 (even lane): the limbs of sum_k (lo_k + mid_k 2^32 + hi_k 2^64)
-        // 2^(32k), k < 8, by two carry chains.  What spills past column 8D+7 (three
-        // words) is the next diagonal's carry: added into slot 8 (the next window's
-        // column 0), or, when squaring, kept apart because the slots get doubled.
-        u32 R[11];
-        add8_shifted(lo, mid, hi, R);
-        if (SQ) {
-            const uint4 sq = ld4(ra + 4 * D);  // a_(4D + k/2) for the even columns (zeros past s)
-            const u32 sqv[4] = {sq.x, sq.y, sq.z, sq.w};
-            double_add_squares(R, sqv);
-            add3_into11(R, cin[0], cin[1], cin[2]);
-            cin[0] = R[8]; cin[1] = R[9]; cin[2] = R[10];
-        } else if (h == 0) {
-            add96(lo[8], mid[8], hi[8], R[8], R[9], R[10]);
-        }
-        if (emit) {
-            const int c0 = 8 * D;
-            if (aligned && c0 + 8 <= out_len) {
-                st4(out + c0, R);
-                st4(out + c0 + 4, R + 4);
-            } else {
-#pragma unroll
-                for (int k = 0; k < 8; ++k)
-                    if (c0 + k < out_len) out[c0 + k] = R[k];
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < 12; ++k) {
-            lo[k] = k + 8 < 12 ? lo[k + 8] : 0u;
-            mid[k] = k + 8 < 12 ? mid[k + 8] : 0u;
-            hi[k] = k + 8 < 12 ? hi[k + 8] : 0u;
-        }
+    // The twelve slots are a ring that advances by eight per diagonal, so three
+    // consecutive diagonals (ring offsets 0, 8, 4) run unrolled with fixed
+    // register names instead of moving the window.
+    PairDiag<SQ> pd{ra, rb, out, T, h, emit, aligned, 2 * s};
+    int D = 0;
+    for (; D + 3 <= 2 * T; D += 3) {
+        pd.template step<0>(D, lo, mid, hi, cin);
+        pd.template step<8>(D + 1, lo, mid, hi, cin);
+        pd.template step<4>(D + 2, lo, mid, hi, cin);
     }
+    if (D < 2 * T) pd.template step<0>(D++, lo, mid, hi, cin);
+    if (D < 2 * T) pd.template step<8>(D++, lo, mid, hi, cin);
 }
 
 // Products at or above this count use the lane-per-product kernels: a lane
