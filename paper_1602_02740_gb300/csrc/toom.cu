@@ -210,11 +210,25 @@ eval_pts_kernel(const u32* __restrict__ in, long in_stride, LevelGeom g, u32* __
     const int npts = 2 * BB - 1;
     const int W = ((N - 1) * N >> 5) + 1;
     const int bw = g.b + W;
-    for (int i = 0; i < BB; ++i)
-        for (int xo = lane; xo < bw; xo += 32) {
-            const int xi = xo - W, gi = i * g.b + xi;
-            rs[pad32(i * bw + xo)] = (xi >= 0 && gi < g.s) ? __ldg(row + gi) : 0u;
-        }
+    // all blocks' limbs of a round are loaded before any is stored, so the global
+    // loads of a row are in flight together
+    for (int r0 = 0; r0 < bw; r0 += 128) {
+        u32 v[BB][4];
+#pragma unroll
+        for (int i = 0; i < BB; ++i)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int xo = r0 + lane + 32 * u, xi = xo - W, gi = i * g.b + xi;
+                v[i][u] = (xo < bw && xi >= 0 && gi < g.s) ? __ldg(row + gi) : 0u;
+            }
+#pragma unroll
+        for (int i = 0; i < BB; ++i)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int xo = r0 + lane + 32 * u;
+                if (xo < bw) rs[pad32(i * bw + xo)] = v[i][u];
+            }
+    }
     __syncwarp();
     auto U = [&](int i, int x) -> u32 {  // limb x of block i (zero outside [0, b))
         return (x >= 0 && x < g.b) ? rs[pad32(i * bw + W + x)] : 0u;
