@@ -1150,14 +1150,22 @@ interp_stream_kernel(InterpArgs a, DivTable dt, FinTable ft, long P) {
             if (lane == 31) { st0[0] = y0[KL - 2]; st0[1] = y0[KL - 1]; }
             st_window<KL>(Wrow(0, 0), base - 2, Y, o);
         }
+        // the rows of node m+1 are loaded while node m is combined
+        u32 pn[KL], qn[KL];
+        ld_seg_masked<KL>(yk + (long)g.ystride, base + KL * lane, len, pn);
+        ld_seg_masked<KL>(yk + 2 * (long)g.ystride, base + KL * lane, len, qn);
         for (int m = 1; m <= n; ++m) {
             // eq. 4.5-4.6: A = W(x) + |W(-x)|, D = W(x) - |W(-x)|, x = 2^(m-1);
             // ce_m = (neg ? D : A) / 2, co_m = x (neg ? A : D) / 2
             u32* s = st0 + 8 * m;
             const bool neg = (negmask >> m) & 1u;
             u32 pv[KL], qv[KL], A[KL], D[KL];
-            ld_seg_masked<KL>(yk + (2 * m - 1) * (long)g.ystride, base + KL * lane, len, pv);
-            ld_seg_masked<KL>(yk + (2 * m) * (long)g.ystride, base + KL * lane, len, qv);
+#pragma unroll
+            for (int j = 0; j < KL; ++j) { pv[j] = pn[j]; qv[j] = qn[j]; }
+            if (m < n) {
+                ld_seg_masked<KL>(yk + (2 * m + 1) * (long)g.ystride, base + KL * lane, len, pn);
+                ld_seg_masked<KL>(yk + (2 * m + 2) * (long)g.ystride, base + KL * lane, len, qn);
+            }
             u32 cA = s[0], bD = s[1];
             const u32 hS[3] = {s[2], s[3], s[4]}, hT[3] = {s[5], s[6], s[7]};
             warp_add_seg<KL>(pv, qv, cA, A);
