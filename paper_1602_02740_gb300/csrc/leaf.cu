@@ -579,29 +579,43 @@ leaf_pair_kernel(const u32* __restrict__ A, long lda, const u32* __restrict__ Bm
     u32* sa = psm + (long)warp * (SQ ? 1 : 2) * 16 * sp;
     u32* sb = SQ ? sa : sa + 16 * sp;
     const long pw = ((long)blockIdx.x * PAIR_WARPS + warp) * 16;  // first product of the warp
-    for (int q = 0; q < 16; ++q) {
-        const long pq = pw + q;
-        const bool ok = pq < P;
-        const u32* ra = A + (ok ? pq : 0) * lda;
-        const u32* rb = Bm + (ok ? pq : 0) * ldb;
-        for (int i = 4 * lane; i < 8 * T; i += 128) {
-            u32 va[4], vb[4];
-            if (ok && vec && i + 4 <= s) {
-                const uint4 x = ld4(ra + i);
-                va[0] = x.x; va[1] = x.y; va[2] = x.z; va[3] = x.w;
-                if (!SQ) {
-                    const uint4 y = ld4(rb + i);
-                    vb[0] = y.x; vb[1] = y.y; vb[2] = y.z; vb[3] = y.w;
-                }
-            } else {
+    if (vec) {
+        // aligned rows: asynchronous 16-byte copies straight into shared memory, all in
+        // flight together; the bytes past a row's end (or of a missing product) are zero
+        for (int q = 0; q < 16; ++q) {
+            const long pq = pw + q;
+            const bool ok = pq < P;
+            const u32* ra = A + (ok ? pq : 0) * lda;
+            const u32* rb = Bm + (ok ? pq : 0) * ldb;
+            for (int i = 4 * lane; i < 8 * T; i += 128) {
+                const int left = ok ? s - i : 0;
+                const unsigned bytes = left >= 4 ? 16u : left > 0 ? 4u * left : 0u;
+                const u32* ga = bytes ? ra + i : ra;
+                const u32* gb = bytes ? rb + i : rb;
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;"
+                             :: "r"((unsigned)__cvta_generic_to_shared(sa + q * sp + i)), "l"(ga), "r"(bytes));
+                if (!SQ)
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;"
+                                 :: "r"((unsigned)__cvta_generic_to_shared(sb + q * sp + i)), "l"(gb), "r"(bytes));
+            }
+        }
+        asm volatile("cp.async.commit_group;\n\tcp.async.wait_all;" ::: "memory");
+    } else {
+        for (int q = 0; q < 16; ++q) {
+            const long pq = pw + q;
+            const bool ok = pq < P;
+            const u32* ra = A + (ok ? pq : 0) * lda;
+            const u32* rb = Bm + (ok ? pq : 0) * ldb;
+            for (int i = 4 * lane; i < 8 * T; i += 128) {
+                u32 va[4], vb[4];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     va[j] = ok && i + j < s ? ra[i + j] : 0u;
                     if (!SQ) vb[j] = ok && i + j < s ? rb[i + j] : 0u;
                 }
+                st4(sa + q * sp + i, va);
+                if (!SQ) st4(sb + q * sp + i, vb);
             }
-            st4(sa + q * sp + i, va);
-            if (!SQ) st4(sb + q * sp + i, vb);
         }
     }
     __syncwarp();
