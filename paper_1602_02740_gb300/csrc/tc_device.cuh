@@ -31,6 +31,17 @@ __device__ __forceinline__ void st4(u32* p, const u32 v[4]) {
     *reinterpret_cast<uint4*>(p) = make_uint4(v[0], v[1], v[2], v[3]);
 }
 
+// Asynchronous 4-byte copy global -> shared (no registers held while in flight);
+// cp_async_wait_all() waits for this thread's copies, a barrier then publishes them.
+__device__ __forceinline__ void cp_async4(u32* dst, const u32* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;"
+                 :: "r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+// all but the most recently committed group complete
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
 // Load 4 limbs starting at index `pos` of a row of `len` valid limbs (zeros
 // beyond).  `pos` is a multiple of 4 and the row base is 16-byte aligned.
 __device__ __forceinline__ void ld4_masked(const u32* row, int pos, int len, u32 v[4]) {

@@ -99,7 +99,7 @@ __host__ __device__ __forceinline__ int pad32(int x) { return x + (x >> 5); }
 __global__ void __launch_bounds__(1024)
 eval_kernel(const u32* __restrict__ in, long in_stride, LevelGeom g, u32* __restrict__ out,
             uint8_t* __restrict__ sgn, long P) {
-    extern __shared__ __align__(16) u32 win[];  // [B][pad32(CH + W)]
+    extern __shared__ __align__(16) u32 win[];  // [2][B][pad32(CH + W) + 1]
     const long k = blockIdx.x;
     if (k >= P) return;
     const u32* row = in + k * in_stride;
@@ -113,6 +113,23 @@ eval_kernel(const u32* __restrict__ in, long in_stride, LevelGeom g, u32* __rest
     const int warp = tid >> 5, lane = tid & 31;
     const int j = warp;             // this warp evaluates x = 2^j (blockDim = 32 max(n, 1))
     const bool has_point = j < g.n;
+    // Chunks of CH output limbs are staged in shared memory by asynchronous copies,
+    // double-buffered: chunk c+1 is in flight while chunk c is summed.
+    const int W = ((g.n - 1) * g.n >> 5) + 1;  // halo: largest limb shift + 1
+    const int wlen = pad32(CH + W) + 1;
+    const int bufw = g.B * wlen;
+    auto stage = [&](int base, u32* buf) {
+        for (int idx = tid; idx < g.B * (CH + W); idx += nt) {
+            const int i = idx / (CH + W), xo = idx - i * (CH + W);
+            const int x = base - W + xo;  // limb index within block i
+            const int gi = i * g.b + x;
+            u32* d = buf + i * wlen + pad32(xo);
+            if (x >= 0 && x < g.b && gi < g.s) cp_async4(d, row + gi);
+            else *d = 0u;
+        }
+        cp_async_commit();
+    };
+    stage(0, win);
     // ---- sign of E - O, top-down (global reads; almost always one window) ----
     int sign = 1;
     if (has_point) {
@@ -139,28 +156,24 @@ eval_kernel(const u32* __restrict__ in, long in_stride, LevelGeom g, u32* __rest
         if (sign == 0) sign = T < 0 ? -1 : 1;
     }
 
-    // ---- bottom-up pass: chunks of CH output limbs staged in shared memory ----
-    const int W = ((g.n - 1) * g.n >> 5) + 1;  // halo: largest limb shift + 1
-    const int wlen = pad32(CH + W) + 1;
+    // ---- bottom-up pass over the staged chunks ----
     u32* rp = out + (k * npts + 2 * j + 1) * (long)g.estride;
     u32* rm = out + (k * npts + 2 * j + 2) * (long)g.estride;
     UnsignedNorm ne{0, 0}, no{0, 0};
     EvalCarry cpm{0, 0};
-    for (int base = 0; base < g.estride; base += CH) {
-        __syncthreads();  // previous chunk's reads are done
-        for (int idx = tid; idx < g.B * (CH + W); idx += nt) {
-            const int i = idx / (CH + W), xo = idx - i * (CH + W);
-            const int x = base - W + xo;  // limb index within block i
-            const int gi = i * g.b + x;
-            win[i * wlen + pad32(xo)] = (x >= 0 && x < g.b && gi < g.s) ? __ldg(row + gi) : 0u;
-        }
+    int c = 0;
+    for (int base = 0; base < g.estride; base += CH, ++c) {
+        const u32* cur = win + (c & 1) * bufw;
+        if (base + CH < g.estride) stage(base + CH, win + ((c + 1) & 1) * bufw);
+        else cp_async_commit();  // one group per chunk: the wait below is for chunk c
+        cp_async_wait_prev();
         __syncthreads();
         if (has_point) {
             u64 e[4] = {0, 0, 0, 0}, o[4] = {0, 0, 0, 0};
             for (int i = 0; i < g.B; ++i) {
                 const int sh = j * i;
                 const int qa = sh >> 5, r = sh & 31;
-                const u32* w = win + i * wlen;
+                const u32* w = cur + i * wlen;
                 // limbs x = 4 lane + jj - qa - 1 .. + 0 of block i, window offset W
                 const int x0 = 4 * lane + W - qa - 1;
                 u32 v[5];
@@ -183,6 +196,7 @@ eval_kernel(const u32* __restrict__ in, long in_stride, LevelGeom g, u32* __rest
                 st4(rm + pos, dm);
             }
         }
+        __syncthreads();  // this buffer is staged again two chunks on
     }
     if (has_point && lane == 0) {
         sgn[k * npts + 2 * j + 1] = 0;
@@ -465,7 +479,7 @@ cudaError_t launch_eval(const u32* in, long in_stride, const LevelGeom& g, u32* 
     }
     const int warps = g.n < 1 ? 1 : g.n;  // n <= 31: one warp per point pair
     const int W = ((g.n - 1) * g.n >> 5) + 1;
-    const size_t smem = (size_t)g.B * ((CH + W) + ((CH + W) >> 5) + 1) * 4;
+    const size_t smem = (size_t)2 * g.B * ((CH + W) + ((CH + W) >> 5) + 1) * 4;  // two chunk buffers
     eval_kernel<<<(unsigned)P, warps * 32, smem, st>>>(in, in_stride, g, out, sgn, P);
     return cudaGetLastError();
 }
