@@ -163,6 +163,29 @@ tc_status tc_mul_uniform_host(tc_ctx *ctx, size_t count, size_t limbs,
                               const uint32_t *A, const uint32_t *Bv, uint32_t *OUT,
                               const tc_opts *opts, void *stream);
 
+/*
+ * Pipelined host-buffer batches (the same products as tc_mul_uniform_host:
+ * `count` rows of `limbs` x `limbs` limbs, packed, results 2*limbs limbs a
+ * row).  The pipe owns device memory for two batches in flight plus the level
+ * scratch, and three streams: copy-in, kernels, copy-out.  tc_pipe_submit
+ * enqueues one batch and returns without waiting: batch i+1's copy-in and
+ * batch i-1's copy-out overlap batch i's kernels.  A, Bv and OUT are HOST
+ * pointers (pinned memory for asynchronous, full-speed copies) that must stay
+ * valid and unmodified (OUT unread) until tc_pipe_wait returns.  `square`
+ * fixes at creation whether batches are squares (Bv ignored, A == Bv
+ * semantics) or products.  tc_pipe_wait blocks until every submitted batch is
+ * complete.  Errors: TC_EINVAL (null or zero arguments, a context of another
+ * device), TC_ENOMEM (the pipe's memory exceeds the context's budget),
+ * TC_EDEVICE.  tc_pipe_destroy waits for the pipe and frees it (NULL ignored).
+ */
+typedef struct tc_pipe tc_pipe;
+tc_status tc_pipe_create(tc_ctx *ctx, size_t count, size_t limbs, int square,
+                         const tc_opts *opts, tc_pipe **out);
+tc_status tc_pipe_submit(tc_ctx *ctx, tc_pipe *pipe, const uint32_t *A, const uint32_t *Bv,
+                         uint32_t *OUT);
+tc_status tc_pipe_wait(tc_pipe *pipe);
+void tc_pipe_destroy(tc_pipe *pipe);
+
 /* ---------------------------------------------------------------------
  * The steps of one Toom level, exported for testing and for callers that
  * schedule levels themselves.  All pointers are device pointers.

@@ -396,6 +396,120 @@ extern "C" tc_status tc_mul_uniform_host(tc_ctx* ctx, size_t count, size_t limbs
 }
 
 // ---------------------------------------------------------------------------
+// Pipelined host-buffer batches: two batches in flight, batch i+1's copy-in and
+// batch i-1's copy-out overlap batch i's kernels.  Three streams ordered by
+// events; device inputs, outputs and level scratch owned by the pipe.
+// ---------------------------------------------------------------------------
+struct tc_pipe {
+    int device = 0;
+    size_t count = 0, limbs = 0;
+    bool square = false;
+    BatchLayout L;
+    char* mem = nullptr;  // level scratch, then per slot: A, B, OUT
+    size_t in_bytes = 0, out_bytes = 0, scratch = 0;
+    cudaStream_t s_in = nullptr, s_run = nullptr, s_out = nullptr;
+    cudaEvent_t in_done[2] = {}, run_done[2] = {}, out_done[2] = {};
+    long submitted = 0;
+    u32* slot_ptr(int slot, int which) const {  // which: 0 A, 1 B, 2 OUT
+        const size_t per = 2 * align256(in_bytes) + align256(out_bytes);
+        char* b = mem + scratch + slot * per;
+        return (u32*)(which == 0 ? b : which == 1 ? b + align256(in_bytes) : b + 2 * align256(in_bytes));
+    }
+};
+
+static void pipe_free(tc_pipe* p) {
+    if (!p) return;
+    cudaSetDevice(p->device);
+    if (p->s_out) cudaStreamSynchronize(p->s_out);
+    for (int i = 0; i < 2; ++i) {
+        if (p->in_done[i]) cudaEventDestroy(p->in_done[i]);
+        if (p->run_done[i]) cudaEventDestroy(p->run_done[i]);
+        if (p->out_done[i]) cudaEventDestroy(p->out_done[i]);
+    }
+    if (p->s_in) cudaStreamDestroy(p->s_in);
+    if (p->s_run) cudaStreamDestroy(p->s_run);
+    if (p->s_out) cudaStreamDestroy(p->s_out);
+    if (p->mem) cudaFree(p->mem);
+    delete p;
+}
+
+extern "C" tc_status tc_pipe_create(tc_ctx* ctx, size_t count, size_t limbs, int square,
+                                    const tc_opts* opts, tc_pipe** out) {
+    if (!ctx || !out || count == 0 || limbs == 0 || limbs > (1u << 30)) return TC_EINVAL;
+    *out = nullptr;
+    CK(cudaSetDevice(ctx->device));
+    tc_opts o;
+    tc_status s = resolve_plan(ctx, limbs, opts, o);
+    if (s) return s;
+    std::unique_ptr<tc_pipe, void (*)(tc_pipe*)> p(new tc_pipe, pipe_free);
+    p->device = ctx->device;
+    p->count = count;
+    p->limbs = limbs;
+    p->square = square != 0;
+    p->L = layout_for(count, limbs, o, p->square);
+    p->scratch = align256(p->L.total);
+    p->in_bytes = count * limbs * 4;
+    p->out_bytes = count * 2 * limbs * 4;
+    const size_t need = p->scratch + 2 * (2 * align256(p->in_bytes) + align256(p->out_bytes));
+    if (need > ctx->budget) return TC_ENOMEM;
+    if (cudaMalloc(&p->mem, need) != cudaSuccess) {
+        cudaGetLastError();
+        p->mem = nullptr;
+        return TC_ENOMEM;
+    }
+    CK(cudaStreamCreateWithFlags(&p->s_in, cudaStreamNonBlocking));
+    CK(cudaStreamCreateWithFlags(&p->s_run, cudaStreamNonBlocking));
+    CK(cudaStreamCreateWithFlags(&p->s_out, cudaStreamNonBlocking));
+    for (int i = 0; i < 2; ++i) {
+        CK(cudaEventCreateWithFlags(&p->in_done[i], cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&p->run_done[i], cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&p->out_done[i], cudaEventDisableTiming));
+    }
+    *out = p.release();
+    return TC_OK;
+}
+
+extern "C" tc_status tc_pipe_submit(tc_ctx* ctx, tc_pipe* p, const uint32_t* A, const uint32_t* Bv,
+                                    uint32_t* OUT) {
+    if (!ctx || !p || !A || !OUT || (!p->square && !Bv)) return TC_EINVAL;
+    if (ctx->device != p->device) return TC_EINVAL;
+    CK(cudaSetDevice(p->device));
+    const int slot = (int)(p->submitted & 1);
+    u32* dA = p->slot_ptr(slot, 0);
+    u32* dB = p->square ? dA : p->slot_ptr(slot, 1);
+    u32* dO = p->slot_ptr(slot, 2);
+    // copy-in: after the kernels of the batch two back stopped reading this slot
+    CK(cudaStreamWaitEvent(p->s_in, p->run_done[slot], 0));
+    CK(cudaMemcpyAsync(dA, A, p->in_bytes, cudaMemcpyHostToDevice, p->s_in));
+    if (!p->square) CK(cudaMemcpyAsync(dB, Bv, p->in_bytes, cudaMemcpyHostToDevice, p->s_in));
+    CK(cudaEventRecord(p->in_done[slot], p->s_in));
+    // kernels: after this batch's copy-in and the copy-out of the batch two back
+    CK(cudaStreamWaitEvent(p->s_run, p->in_done[slot], 0));
+    CK(cudaStreamWaitEvent(p->s_run, p->out_done[slot], 0));
+    tc_status s = run_uniform(p->L, p->mem, p->count, p->limbs, dA, (long)p->limbs, dB,
+                              (long)p->limbs, dO, (long)(2 * p->limbs), p->square, p->s_run, ctx);
+    if (s) return s;
+    CK(cudaEventRecord(p->run_done[slot], p->s_run));
+    // copy-out
+    CK(cudaStreamWaitEvent(p->s_out, p->run_done[slot], 0));
+    CK(cudaMemcpyAsync(OUT, dO, p->out_bytes, cudaMemcpyDeviceToHost, p->s_out));
+    CK(cudaEventRecord(p->out_done[slot], p->s_out));
+    ++p->submitted;
+    return TC_OK;
+}
+
+extern "C" tc_status tc_pipe_wait(tc_pipe* p) {
+    if (!p) return TC_EINVAL;
+    CK(cudaSetDevice(p->device));
+    CK(cudaStreamSynchronize(p->s_out));  // its last copy waits on every earlier step
+    CK(cudaStreamSynchronize(p->s_run));
+    CK(cudaStreamSynchronize(p->s_in));
+    return TC_OK;
+}
+
+extern "C" void tc_pipe_destroy(tc_pipe* p) { pipe_free(p); }
+
+// ---------------------------------------------------------------------------
 // General products: gather into padded rows per size class, run, scatter.
 // ---------------------------------------------------------------------------
 namespace {

@@ -69,6 +69,11 @@ _SIGS = {
     "tc_batch_destroy": (None, [_vp]),
     "tc_mul_uniform": (ctypes.c_int, [_vp, _sz, _sz, _u32p, _sz, _u32p, _sz, _u32p, _sz, _optp, _vp]),
     "tc_mul_uniform_host": (ctypes.c_int, [_vp, _sz, _sz, _u32p, _u32p, _u32p, _optp, _vp]),
+    "tc_pipe_create": (ctypes.c_int, [_vp, _sz, _sz, ctypes.c_int, _optp,
+                                      ctypes.POINTER(ctypes.c_void_p)]),
+    "tc_pipe_submit": (ctypes.c_int, [_vp, _vp, _u32p, _u32p, _u32p]),
+    "tc_pipe_wait": (ctypes.c_int, [_vp]),
+    "tc_pipe_destroy": (None, [_vp]),
     "tc_schoolbook": (ctypes.c_int, [_sz, _sz, _u32p, _sz, _u32p, _sz, _u32p, _sz, _vp]),
     "tc_toom_evaluate": (ctypes.c_int, [_sz, _sz, ctypes.c_int, _u32p, _sz, _u32p, _sz, _u8p, _vp]),
     "tc_toom_interpolate": (ctypes.c_int, [_sz, _sz, ctypes.c_int, _u32p, _sz, _u8p, _u8p, _u32p,
@@ -232,6 +237,53 @@ def tc_mul_uniform_host(ctx: Context, A, B, OUT, plan=None, stream=None):
     _check(lib().tc_mul_uniform_host(ctx.handle, count, L, _ptr(A), _ptr(B), _ptr(OUT),
                                      _opts(plan), _stream(stream)), "tc_mul_uniform_host")
     return OUT
+
+
+class Pipe:
+    """Pipelined host-buffer batches (tc_pipe_*): two batches in flight, copies
+    overlapping the kernels.  Host buffers handed to submit() must stay alive and
+    untouched until wait() returns."""
+
+    def __init__(self, ctx: Context, count: int, limbs: int, square: bool = False, plan=None):
+        self.ctx = ctx
+        self.count, self.limbs, self.square = count, limbs, square
+        h = ctypes.c_void_p()
+        _check(lib().tc_pipe_create(ctx.handle, count, limbs, 1 if square else 0, _opts(plan),
+                                    ctypes.byref(h)), "tc_pipe_create")
+        self.handle = h.value
+        self._held = []
+
+    def submit(self, A, B, OUT):
+        """A, B (count, limbs) and OUT (count, 2 limbs): contiguous host tensors/arrays."""
+        for x, cols in ((A, self.limbs), (OUT, 2 * self.limbs)) + (() if self.square else ((B, self.limbs),)):
+            if tuple(x.shape) != (self.count, cols):
+                raise ValueError(f"shape {tuple(x.shape)} != {(self.count, cols)}")
+            if not (x.flags.c_contiguous if isinstance(x, np.ndarray) else x.is_contiguous()):
+                raise ValueError("pipe buffers must be contiguous")
+        self._held.append((A, B, OUT))
+        _check(lib().tc_pipe_submit(self.ctx.handle, self.handle, _ptr(A),
+                                    _ptr(A if self.square else B), _ptr(OUT)), "tc_pipe_submit")
+        return OUT
+
+    def wait(self):
+        _check(lib().tc_pipe_wait(self.handle), "tc_pipe_wait")
+        self._held.clear()
+
+    def close(self):
+        if self.handle:
+            lib().tc_pipe_destroy(self.handle)
+            self.handle = None
+            self._held.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def tc_pipe_create(ctx: Context, count: int, limbs: int, square: bool = False, plan=None) -> Pipe:
+    return Pipe(ctx, count, limbs, square, plan)
 
 
 def tc_mul_batch(ctx: Context, A, a_off, a_len, B, b_off, b_len, OUT, out_off, plan=None,

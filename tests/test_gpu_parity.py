@@ -206,6 +206,46 @@ def test_host_entry_point(ctx, tc):
         assert same_limbs(OUT[k], to_int(A[k]) * to_int(B[k]))
 
 
+@pytest.mark.parametrize("square", [False, True])
+def test_pipe_batches_in_flight(ctx, tc, square):
+    """Five batches submitted back to back (two in flight, copies overlapping
+    the kernels): every product exact, each batch in its own output buffer."""
+    import torch
+    L, count, nb = 2731, 6, 5
+    As = [np.stack([inputs.uniform(L, 1000 * i + k) for k in range(count)]) for i in range(nb)]
+    Bs = As if square else [np.stack([inputs.uniform(L, 1000 * i + 500 + k) for k in range(count)])
+                            for i in range(nb)]
+    hA = [torch.from_numpy(a.view(np.int32)).pin_memory() for a in As]
+    hB = hA if square else [torch.from_numpy(b.view(np.int32)).pin_memory() for b in Bs]
+    hO = [torch.zeros((count, 2 * L), dtype=torch.int32).pin_memory() for _ in range(nb)]
+    pipe = tc.tc.tc_pipe_create(ctx, count, L, square=square)
+    for i in range(nb):
+        pipe.submit(hA[i], hB[i], hO[i])
+    pipe.wait()
+    # and again into the same buffers: results unchanged
+    for i in range(nb):
+        pipe.submit(hA[i], hB[i], hO[i])
+    pipe.wait()
+    pipe.close()
+    for i in range(nb):
+        out = hO[i].numpy().view(np.uint32)
+        for k in range(count):
+            assert same_limbs(out[k], to_int(As[i][k]) * to_int(Bs[i][k]))
+
+
+def test_pipe_rejects_bad_input(ctx, tc):
+    t = tc.tc
+    with pytest.raises(t.TCError):
+        t.tc_pipe_create(ctx, 0, 100)
+    with pytest.raises(t.TCError):
+        t.tc_pipe_create(ctx, 4, 0)
+    pipe = t.tc_pipe_create(ctx, 2, 64)
+    with pytest.raises(ValueError):
+        pipe.submit(np.zeros((3, 64), np.uint32), np.zeros((2, 64), np.uint32),
+                    np.zeros((2, 128), np.uint32))
+    pipe.close()
+
+
 def test_batch_mixed_sizes(ctx, tc):
     la, lb = inputs.batch_lengths(120, seed=4, lo=64, hi=6000)
     a_off = np.concatenate([[0], np.cumsum(la)[:-1]])
