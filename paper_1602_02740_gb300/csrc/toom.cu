@@ -211,7 +211,7 @@ eval_kernel(const u32* __restrict__ in, long in_stride, LevelGeom g, u32* __rest
 // serve all points x = 2^j (column sums for every j from the same registers),
 // and the top-down sign scans of all points share their loads.
 template <int BB>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, BB <= 4 ? 4 : 1)
 eval_pts_kernel(const u32* __restrict__ in, long in_stride, LevelGeom g, u32* __restrict__ out,
                 uint8_t* __restrict__ sgn, long P, int rowlen) {
     constexpr int N = BB - 1;
