@@ -96,7 +96,8 @@ __device__ __forceinline__ void eval_finish(const u64 e[4], const u64 o[4], int 
 // 4t + c conflict-free.
 __host__ __device__ __forceinline__ int pad32(int x) { return x + (x >> 5); }
 
-__global__ void __launch_bounds__(1024)
+template <int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB)
 eval_kernel(const u32* __restrict__ in, long in_stride, LevelGeom g, u32* __restrict__ out,
             uint8_t* __restrict__ sgn, long P) {
     extern __shared__ __align__(16) u32 win[];  // [2][B][pad32(CH + W) + 1]
@@ -106,8 +107,6 @@ eval_kernel(const u32* __restrict__ in, long in_stride, LevelGeom g, u32* __rest
     const int npts = 2 * g.B - 1;
     u32* orow0 = out + (k * npts) * (long)g.estride;
     const int tid = threadIdx.x, nt = blockDim.x;
-    // point 0: U(0) = u_0
-    for (int i = tid; i < g.estride; i += nt) orow0[i] = (i < g.b && i < g.s) ? row[i] : 0u;
     if (tid == 0) sgn[k * npts] = 0;
 
     const int warp = tid >> 5, lane = tid & 31;
@@ -118,14 +117,25 @@ eval_kernel(const u32* __restrict__ in, long in_stride, LevelGeom g, u32* __rest
     const int W = ((g.n - 1) * g.n >> 5) + 1;  // halo: largest limb shift + 1
     const int wlen = pad32(CH + W) + 1;
     const int bufw = g.B * wlen;
+    // staging map, fixed for the kernel: thread -> window offsets xo (one when the
+    // block has a window's width of threads) and blocks i0, i0 + istep, ...
+    const int span = CH + W;
+    const bool wide_blk = nt >= span;
+    const int istep = wide_blk ? nt / span : 1;
+    const int xo0 = wide_blk ? tid % span : tid, xstep = wide_blk ? span : nt;
+    const int i0 = wide_blk ? tid / span : 0;
     auto stage = [&](int base, u32* buf) {
-        for (int idx = tid; idx < g.B * (CH + W); idx += nt) {
-            const int i = idx / (CH + W), xo = idx - i * (CH + W);
-            const int x = base - W + xo;  // limb index within block i
-            const int gi = i * g.b + x;
-            u32* d = buf + i * wlen + pad32(xo);
-            if (x >= 0 && x < g.b && gi < g.s) cp_async4(d, row + gi);
-            else *d = 0u;
+        if (i0 < istep) {
+            for (int xo = xo0; xo < span; xo += xstep) {
+                const int x = base - W + xo;  // limb index within each block
+                const bool inb = x >= 0 && x < g.b;
+                int gi = i0 * g.b + x;
+                u32* d = buf + i0 * wlen + pad32(xo);
+                for (int i = i0; i < g.B; i += istep, gi += istep * g.b, d += istep * wlen) {
+                    if (inb && gi < g.s) cp_async4(d, row + gi);
+                    else *d = 0u;
+                }
+            }
         }
         cp_async_commit();
     };
@@ -168,22 +178,27 @@ eval_kernel(const u32* __restrict__ in, long in_stride, LevelGeom g, u32* __rest
         else cp_async_commit();  // one group per chunk: the wait below is for chunk c
         cp_async_wait_prev();
         __syncthreads();
+        // point 0: U(0) = u_0, block 0 of the staged chunk (zero past b and s)
+        for (int x = tid; x < CH && base + x < g.estride; x += nt) orow0[base + x] = cur[pad32(W + x)];
         if (has_point) {
             u64 e[4] = {0, 0, 0, 0}, o[4] = {0, 0, 0, 0};
-            for (int i = 0; i < g.B; ++i) {
+            // block i shifted left by j i bits: limbs x = 4 lane + jj - qa - 1 .. + 0 of
+            // block i (window offset W), added into E (i even) or O (i odd)
+            auto add_block = [&](int i, u64 acc[4]) {
                 const int sh = j * i;
-                const int qa = sh >> 5, r = sh & 31;
+                const int qa = sh >> 5;
+                const u32 r = (u32)(sh & 31);
                 const u32* w = cur + i * wlen;
-                // limbs x = 4 lane + jj - qa - 1 .. + 0 of block i, window offset W
                 const int x0 = 4 * lane + W - qa - 1;
                 u32 v[5];
 #pragma unroll
                 for (int q = 0; q < 5; ++q) v[q] = w[pad32(x0 + q)];
 #pragma unroll
-                for (int jj = 0; jj < 4; ++jj) {
-                    const u32 t = fshl(v[jj], v[jj + 1], (u32)r);
-                    if (i & 1) o[jj] += t; else e[jj] += t;
-                }
+                for (int jj = 0; jj < 4; ++jj) acc[jj] += fshl(v[jj], v[jj + 1], r);
+            };
+            for (int i = 0; i < g.B; i += 2) {
+                add_block(i, e);
+                if (i + 1 < g.B) add_block(i + 1, o);
             }
 #pragma unroll
             for (int jj = 0; jj < 4; ++jj)
@@ -480,7 +495,10 @@ cudaError_t launch_eval(const u32* in, long in_stride, const LevelGeom& g, u32* 
     const int warps = g.n < 1 ? 1 : g.n;  // n <= 31: one warp per point pair
     const int W = ((g.n - 1) * g.n >> 5) + 1;
     const size_t smem = (size_t)2 * g.B * ((CH + W) + ((CH + W) >> 5) + 1) * 4;  // two chunk buffers
-    eval_kernel<<<(unsigned)P, warps * 32, smem, st>>>(in, in_stride, g, out, sgn, P);
+    if (warps * 32 <= 384)  // up to B = 13: three blocks per SM (at most 56 registers)
+        eval_kernel<384, 3><<<(unsigned)P, warps * 32, smem, st>>>(in, in_stride, g, out, sgn, P);
+    else
+        eval_kernel<1024, 1><<<(unsigned)P, warps * 32, smem, st>>>(in, in_stride, g, out, sgn, P);
     return cudaGetLastError();
 }
 
