@@ -1358,24 +1358,28 @@ interp_stream_kernel(InterpArgs a, DivTable dt, FinTable ft, long P) {
     UnsignedNorm nst{0, 0};
     const int nterms = 2 * n + 1;
     for (int base_l = 0; base_l < a.out_len; base_l += CH) {
-        u64 cols[4];
+        u64 cols[4] = {0, 0, 0, 0};
         const int l0 = base_l + 4 * lane;
-        const int t0 = l0 / g.b;
+        if (l0 < a.out_len) {
+            // terms t with 0 <= l - t b < Y for some l in [l0, l0 + 4), highest first
+            int t = (l0 + 3) / g.b;
+            if (t > nterms - 1) t = nterms - 1;
+            for (; t >= 0; --t) {
+                const int x = l0 - t * g.b;
+                if (x >= Y) break;
+                const u32* w = Wrow(t & 1, (t + 1) >> 1);
+                if (x >= 0 && x + 4 <= Y && ((x & 3) == 0)) {
+                    const uint4 q = ld4(w + x);
+                    cols[0] += q.x; cols[1] += q.y; cols[2] += q.z; cols[3] += q.w;
+                } else {
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int l = l0 + j;
-            u64 S = 0;
-            if (l < a.out_len) {
-                int t = t0;
-                while ((t + 1) * g.b <= l) ++t;  // t = floor(l / b)
-                if (t > nterms - 1) t = nterms - 1;
-                for (; t >= 0; --t) {
-                    const int x = l - t * g.b;
-                    if (x >= Y) break;
-                    S += Wrow(t & 1, (t + 1) >> 1)[x];
+                    for (int j = 0; j < 4; ++j)
+                        if (x + j >= 0 && x + j < Y) cols[j] += w[x + j];
                 }
             }
-            cols[j] = S;
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (l0 + j >= a.out_len) cols[j] = 0;
         }
         u32 d[4];
         warp_norm_unsigned(cols, nst, d);
