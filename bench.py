@@ -46,7 +46,7 @@ IMAD_PER_LIMB_PRODUCT = 2  # low and high halves of a 32 x 32 -> 64-bit product
 # leaf_pair_kernel<false> on 269192 products of 116 limbs moved 4.5072e8 bytes
 # (dram__bytes_read.sum + dram__bytes_write.sum); traffic grows with the number
 # of products, so a launch of N such products moves N * 1674 bytes.
-LEAF_TRAFFIC = {"kernel": "leaf_pair_kernel<false>", "limbs": 116, "bytes_per_product": 4.5072e8 / 269192}
+LEAF_TRAFFIC = {"kernel": "leaf_pair_kernel<false>", "limbs": 116, "bytes_per_product": 4.50208256e8 / 269192}
 
 
 def parse():
