@@ -37,6 +37,11 @@ __device__ __forceinline__ void cp_async4(u32* dst, const u32* src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;"
                  :: "r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src) : "memory");
 }
+// Asynchronous 16-byte copy global -> shared (both addresses 16-byte aligned).
+__device__ __forceinline__ void cp_async16(u32* dst, const u32* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
+                 :: "r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 // all but the most recently committed group complete

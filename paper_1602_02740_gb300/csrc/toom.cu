@@ -1306,12 +1306,11 @@ interp_stream_kernel(InterpArgs a, DivTable dt, FinTable ft, long P) {
     // ---- pass B: Newton to monomial basis (Theorem 3.3), aligned windows ----
     for (int base = 0; base < Y; base += C) {
         __syncwarp();
+        // the window of every value, all copies in flight together
         for (int p = 0; p < 2; ++p)
-            for (int m = 1; m <= n; ++m) {
-                u32 v[KL];
-                ld_seg<KL>(Wrow(p, m) + base + KL * lane, v);
-                st_seg<KL>(V(p, m), v);
-            }
+            for (int m = 1; m <= n; ++m) cp_async16(V(p, m), Wrow(p, m) + base + KL * lane);
+        cp_async_wait_all();
+        __syncwarp();
         // in place with kx ascending (each update reads the old c_(kx+1))
         int t2 = 0;  // index of chain (m, m)
         for (int m = n - 1; m >= 1; --m) {
@@ -1489,16 +1488,35 @@ interp_reg_kernel(InterpArgs a, DivTable dt, long P) {
         if (a.sv) s ^= a.sv[k * npts + p] != 0;
         return s;
     };
+    // Shared memory: 2N+1 slots of C + 4 words; first the input rows (all copies in
+    // flight together, zero past the 2e valid limbs), at the end the recomposed terms.
+    constexpr int SLOT = C + 4;
+    u32* sw = sm + (long)warp * (2 * N + 1) * SLOT;
+#pragma unroll
+    for (int r = 0; r <= 2 * N; ++r) {
+        const u32* row = yk + r * (long)g.ystride;
+#pragma unroll
+        for (int jj = 0; jj < KL; jj += 4) {
+            const int pos = KL * lane + jj;
+            const int left = len - pos;
+            const unsigned bytes = left >= 4 ? 16u : left > 0 ? 4u * left : 0u;
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;"
+                         :: "r"((unsigned)__cvta_generic_to_shared(sw + r * SLOT + pos)),
+                            "l"(bytes ? row + pos : row), "r"(bytes) : "memory");
+        }
+    }
+    cp_async_wait_all();
+    __syncwarp();
     u32 c[2][N + 1][KL];
     // ---- even-odd combine (eq. 4.5-4.6) ----
-    ld_seg_masked<KL>(yk, KL * lane, len, c[0][0]);
+    ld_seg<KL>(sw + KL * lane, c[0][0]);
 #pragma unroll
     for (int j = 0; j < KL; ++j) c[1][0][j] = 0;
 #pragma unroll
     for (int m = 1; m <= N; ++m) {
         u32 pv[KL], qv[KL], A[KL], D[KL];
-        ld_seg_masked<KL>(yk + (2 * m - 1) * (long)g.ystride, KL * lane, len, pv);
-        ld_seg_masked<KL>(yk + (2 * m) * (long)g.ystride, KL * lane, len, qv);
+        ld_seg<KL>(sw + (2 * m - 1) * SLOT + KL * lane, pv);
+        ld_seg<KL>(sw + (2 * m) * SLOT + KL * lane, qv);
         u32 z = 0;
         warp_add_seg<KL>(pv, qv, z, A);
         z = 0;
@@ -1553,8 +1571,7 @@ interp_reg_kernel(InterpArgs a, DivTable dt, long P) {
     // Term t (w_2i = ce_i, w_2i+1 = co_(i+1)) is stored shifted by d_t = (t b) mod 4
     // words inside a slot of C + 4 words, so limb l - t b of it sits at a 16-byte
     // aligned index whenever l is a multiple of 4: one vector load per term per lane.
-    constexpr int SLOT = C + 4;
-    u32* sw = sm + (long)warp * (2 * N + 1) * SLOT;
+    __syncwarp();  // every lane has read its input rows
     const int b = g.b;
 #pragma unroll
     for (int t = 0; t <= 2 * N; ++t) {
