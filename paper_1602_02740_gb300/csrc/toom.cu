@@ -1360,21 +1360,38 @@ interp_stream_kernel(InterpArgs a, DivTable dt, FinTable ft, long P) {
         u64 cols[4] = {0, 0, 0, 0};
         const int l0 = base_l + 4 * lane;
         if (l0 < a.out_len) {
-            // terms t with 0 <= l - t b < Y for some l in [l0, l0 + 4), highest first
+            // terms t with 0 <= l - t b < Y for some l in [l0, l0 + 4), highest first;
+            // the first four are loaded before any is added (their loads overlap)
             int t = (l0 + 3) / g.b;
             if (t > nterms - 1) t = nterms - 1;
-            for (; t >= 0; --t) {
-                const int x = l0 - t * g.b;
-                if (x >= Y) break;
-                const u32* w = Wrow(t & 1, (t + 1) >> 1);
+            auto load_term = [&](int tt, u32 q[4]) {
+                const int x = l0 - tt * g.b;
+                const u32* w = Wrow(tt & 1, (tt + 1) >> 1);
                 if (x >= 0 && x + 4 <= Y && ((x & 3) == 0)) {
-                    const uint4 q = ld4(w + x);
-                    cols[0] += q.x; cols[1] += q.y; cols[2] += q.z; cols[3] += q.w;
+                    const uint4 v = ld4(w + x);
+                    q[0] = v.x; q[1] = v.y; q[2] = v.z; q[3] = v.w;
                 } else {
 #pragma unroll
-                    for (int j = 0; j < 4; ++j)
-                        if (x + j >= 0 && x + j < Y) cols[j] += w[x + j];
+                    for (int j = 0; j < 4; ++j) q[j] = x + j >= 0 && x + j < Y ? w[x + j] : 0u;
                 }
+            };
+            u32 q[4][4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const bool act = t - i >= 0 && l0 - (t - i) * g.b < Y;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) q[i][j] = 0;
+                if (act) load_term(t - i, q[i]);
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) cols[j] += q[i][j];
+            for (t -= 4; t >= 0 && l0 - t * g.b < Y; --t) {
+                u32 r[4];
+                load_term(t, r);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) cols[j] += r[j];
             }
 #pragma unroll
             for (int j = 0; j < 4; ++j)
