@@ -1356,47 +1356,55 @@ interp_stream_kernel(InterpArgs a, DivTable dt, FinTable ft, long P) {
     const bool aligned = ((reinterpret_cast<uintptr_t>(out) & 15u) == 0);
     UnsignedNorm nst{0, 0};
     const int nterms = 2 * n + 1;
+    // Terms t with 0 <= l - t b < Y for some l in [l0, l0 + 4), highest first.  The
+    // first four of a chunk are loaded before any is added, and those of chunk c+1
+    // while chunk c is normalised (software pipelined); more terms (short b) follow
+    // in a plain loop.
+    auto load_term = [&](int l0, int tt, u32 q[4]) {
+        const int x = l0 - tt * g.b;
+        const u32* w = Wrow(tt & 1, (tt + 1) >> 1);
+        if (x >= 0 && x + 4 <= Y && ((x & 3) == 0)) {
+            const uint4 v = ld4(w + x);
+            q[0] = v.x; q[1] = v.y; q[2] = v.z; q[3] = v.w;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) q[j] = x + j >= 0 && x + j < Y ? w[x + j] : 0u;
+        }
+    };
+    auto issue = [&](int l0, u32 q[4][4], int& trest) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) q[i][j] = 0;
+        trest = -1;
+        if (l0 >= a.out_len) return;
+        int t = (l0 + 3) / g.b;
+        if (t > nterms - 1) t = nterms - 1;
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            if (t - i >= 0 && l0 - (t - i) * g.b < Y) load_term(l0, t - i, q[i]);
+        trest = t - 4;
+    };
+    u32 qn[4][4];
+    int tn;
+    issue(4 * lane, qn, tn);
     for (int base_l = 0; base_l < a.out_len; base_l += CH) {
         u64 cols[4] = {0, 0, 0, 0};
         const int l0 = base_l + 4 * lane;
-        if (l0 < a.out_len) {
-            // terms t with 0 <= l - t b < Y for some l in [l0, l0 + 4), highest first;
-            // the first four are loaded before any is added (their loads overlap)
-            int t = (l0 + 3) / g.b;
-            if (t > nterms - 1) t = nterms - 1;
-            auto load_term = [&](int tt, u32 q[4]) {
-                const int x = l0 - tt * g.b;
-                const u32* w = Wrow(tt & 1, (tt + 1) >> 1);
-                if (x >= 0 && x + 4 <= Y && ((x & 3) == 0)) {
-                    const uint4 v = ld4(w + x);
-                    q[0] = v.x; q[1] = v.y; q[2] = v.z; q[3] = v.w;
-                } else {
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) q[j] = x + j >= 0 && x + j < Y ? w[x + j] : 0u;
-                }
-            };
-            u32 q[4][4];
+        for (int i = 0; i < 4; ++i)
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const bool act = t - i >= 0 && l0 - (t - i) * g.b < Y;
+            for (int j = 0; j < 4; ++j) cols[j] += qn[i][j];
+        for (int t = tn; t >= 0 && l0 - t * g.b < Y; --t) {
+            u32 r[4];
+            load_term(l0, t, r);
 #pragma unroll
-                for (int j = 0; j < 4; ++j) q[i][j] = 0;
-                if (act) load_term(t - i, q[i]);
-            }
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) cols[j] += q[i][j];
-            for (t -= 4; t >= 0 && l0 - t * g.b < Y; --t) {
-                u32 r[4];
-                load_term(t, r);
-#pragma unroll
-                for (int j = 0; j < 4; ++j) cols[j] += r[j];
-            }
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-                if (l0 + j >= a.out_len) cols[j] = 0;
+            for (int j = 0; j < 4; ++j) cols[j] += r[j];
         }
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (l0 + j >= a.out_len) cols[j] = 0;
+        issue(l0 + CH, qn, tn);
         u32 d[4];
         warp_norm_unsigned(cols, nst, d);
         if (aligned && l0 + 4 <= a.out_len) {
