@@ -164,10 +164,12 @@ tc_status tc_mul_uniform_host(tc_ctx *ctx, size_t count, size_t limbs,
                               const tc_opts *opts, void *stream);
 
 /*
- * Pipelined host-buffer batches (the same products as tc_mul_uniform_host:
- * `count` rows of `limbs` x `limbs` limbs, packed, results 2*limbs limbs a
- * row).  The pipe owns device memory for two batches in flight plus the level
- * scratch, and three streams: copy-in, kernels, copy-out.  tc_pipe_submit
+ * Pipelined host-buffer batches (the same products as tc_mul_uniform_host,
+ * Section 1 with the context's plan: `count` rows of `limbs` x `limbs` limbs,
+ * packed, results 2*limbs limbs a row; the pipelining is scheduling only).
+ * The pipe owns device memory for two batches in flight plus its own level
+ * scratch (so its batches do not contend with other calls on the context for
+ * the context's scratch), and three streams: copy-in, kernels, copy-out.  tc_pipe_submit
  * enqueues one batch and returns without waiting: batch i+1's copy-in and
  * batch i-1's copy-out overlap batch i's kernels.  A, Bv and OUT are HOST
  * pointers (pinned memory for asynchronous, full-speed copies) that must stay
