@@ -1734,10 +1734,20 @@ cudaError_t launch_interp(const LevelGeom& g, const u32* y, const uint8_t* su, c
             });
             const FinTable& ft = fins[g.n];
             const int per_warp = stream_layout(g.n, 128, ft.off[g.n + 1]).words * 4;
+            // registers per warp as allocated (per thread rounded up to 8)
+            static int regs_per_warp = 0;
+            static std::once_flag regs_once;
+            std::call_once(regs_once, [] {
+                cudaFuncAttributes fa;
+                regs_per_warp = cudaFuncGetAttributes(&fa, interp_stream_kernel) == cudaSuccess
+                                    ? (fa.numRegs + 7) / 8 * 8 * 32 : 64 * 32;
+            });
             int best_w = 1, best_res = 0;
             for (int w = 1; w <= 8; ++w) {
                 if (w * per_warp > STREAM_SMEM_MAX) break;
                 int blocks = SM_SMEM_BYTES / (w * per_warp + 1024);
+                const int reg_blocks = 65536 / (w * regs_per_warp);
+                if (blocks > reg_blocks) blocks = reg_blocks;
                 if (blocks > 32) blocks = 32;
                 int res = blocks * w;
                 if (res > 64) res = 64;
