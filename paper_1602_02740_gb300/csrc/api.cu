@@ -420,7 +420,8 @@ struct tc_pipe {
 static void pipe_free(tc_pipe* p) {
     if (!p) return;
     cudaSetDevice(p->device);
-    if (p->s_out) cudaStreamSynchronize(p->s_out);
+    for (cudaStream_t s : {p->s_in, p->s_run, p->s_out})
+        if (s) cudaStreamSynchronize(s);
     for (int i = 0; i < 2; ++i) {
         if (p->in_done[i]) cudaEventDestroy(p->in_done[i]);
         if (p->run_done[i]) cudaEventDestroy(p->run_done[i]);
