@@ -55,3 +55,21 @@ def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(tc, "_lib", None)
     with pytest.raises(RuntimeError, match="missing"):
         tc.lib()
+
+
+def test_host_argument_checks_without_gpu(libtc):
+    """Null handles and sizes are rejected on the host (TC_EINVAL) before any CUDA
+    call, so these run on a machine without a GPU."""
+    vp = ctypes.c_void_p
+    h = vp()
+    libtc.tc_pipe_create.argtypes = [vp, ctypes.c_size_t, ctypes.c_size_t, ctypes.c_int, vp,
+                                     ctypes.POINTER(vp)]
+    assert libtc.tc_pipe_create(None, 4, 64, 0, None, ctypes.byref(h)) == -1
+    libtc.tc_pipe_submit.argtypes = [vp, vp, vp, vp, vp]
+    assert libtc.tc_pipe_submit(None, None, None, None, None) == -1
+    libtc.tc_pipe_wait.argtypes = [vp]
+    assert libtc.tc_pipe_wait(None) == -1
+    libtc.tc_pipe_destroy.argtypes = [vp]
+    libtc.tc_pipe_destroy(None)
+    libtc.tc_batch_destroy.argtypes = [vp]
+    libtc.tc_batch_destroy(None)
