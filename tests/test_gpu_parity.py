@@ -171,6 +171,54 @@ def test_square_vs_oracle(ctx, tc, L, plan):
     assert np.array_equal(out, out2)
 
 
+def _degenerate(kind, L, seed):
+    a = np.zeros(L, np.uint32)
+    if kind == "zero":
+        pass
+    elif kind == "one":
+        a[0] = 1
+    elif kind == "top_bit":        # 2^(32 L - 1): only the last block is nonzero
+        a[-1] = 0x80000000
+    elif kind == "top_limb":
+        a[-1] = 0xFFFFFFFF
+    elif kind == "zero_blocks":    # every other 1/12 of the limbs zero (whole blocks vanish)
+        a[:] = inputs.uniform(L, seed)
+        step = max(1, L // 12)
+        for i in range(0, L, 2 * step):
+            a[i:i + step] = 0
+    else:
+        a[:] = inputs.uniform(L, seed)
+    return a
+
+
+@pytest.mark.parametrize("L,plan", [(3000, [4, 3]), (32768, [12, 6, 4]), (32768, [16, 8, 4])])
+@pytest.mark.parametrize("ka,kb", [("zero", "uniform"), ("uniform", "zero"), ("zero", "zero"),
+                                   ("one", "uniform"), ("top_bit", "top_bit"),
+                                   ("top_limb", "uniform"), ("zero_blocks", "zero_blocks"),
+                                   ("zero_blocks", "top_bit")])
+def test_degenerate_operands(ctx, tc, L, plan, ka, kb):
+    """Zero operands, one, a single top bit, whole zero blocks: the evaluation's
+    sign cases (U(-x) = 0, E = O) and empty pointwise products, limb-exact."""
+    a = _degenerate(ka, L, 7)
+    b = _degenerate(kb, L, 8)
+    out = host(tc.tc.tc_mul(ctx, dev(a), dev(b), plan=plan))
+    assert same_limbs(out, to_int(a) * to_int(b))
+    if ka == kb:
+        out2 = host(tc.tc.tc_sqr(ctx, dev(a), plan=plan))
+        assert same_limbs(out2, to_int(a) ** 2)
+
+
+def test_degenerate_rows_in_a_batch(ctx, tc):
+    """A batch whose rows mix degenerate and uniform operands (one launch per level)."""
+    L = 4096
+    kinds = ["zero", "one", "top_bit", "top_limb", "zero_blocks", "uniform"] * 2
+    A = np.stack([_degenerate(k, L, 20 + i) for i, k in enumerate(kinds)])
+    B = np.stack([_degenerate(kinds[(i + 3) % len(kinds)], L, 40 + i) for i in range(len(kinds))])
+    OUT = host(tc.tc.tc_mul_uniform(ctx, dev(A), dev(B), plan=[8, 4]))
+    for k in range(len(kinds)):
+        assert same_limbs(OUT[k], to_int(A[k]) * to_int(B[k])), k
+
+
 @pytest.mark.parametrize("na,nb", [(1, 7), (7, 1), (100, 150), (150, 100), (300, 1200),
                                    (5000, 1234), (64, 65536), (1, 1), (3, 0), (0, 5)])
 def test_unbalanced_and_empty(ctx, tc, na, nb):
