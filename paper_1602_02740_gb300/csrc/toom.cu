@@ -573,6 +573,9 @@ static DivConst make_div(u32 d, int KL) {
     return c;
 }
 
+// The same constants for other translation units (the matrix interpolation).
+DivConst make_div_const(u32 d, int KL) { return make_div(d, KL); }
+
 static DivTable make_div_table(int KL) {
     DivTable t;
     for (int k = 0; k < 32; ++k) {

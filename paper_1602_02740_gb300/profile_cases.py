@@ -10,10 +10,11 @@ to a few GB, so a full `ncu` capture of one launch ends quickly.
   python -m paper_1602_02740_gb300.profile_cases leaf --count 157320 --limbs 184
   python -m paper_1602_02740_gb300.profile_cases eval --count 2432 --limbs 32768 --B 12
 
-interp: one Toom level's interpolation (tc_toom_interpolate) of `count`
-        products of `limbs`-limb operands split into B blocks; its inputs are
-        the true pointwise products (evaluation, then products of the
-        evaluations through tc_mul_uniform).
+interp: one Toom level's interpolation (tc_toom_interpolate, or with
+        --method matrix tc_toom_interpolate_matrix) of `count` products of
+        `limbs`-limb operands split into B blocks; its inputs are the true
+        pointwise products (evaluation, then products of the evaluations
+        through tc_mul_uniform).
 leaf:   the batched schoolbook (tc_schoolbook) of `count` products.
 eval:   one level's evaluation (tc_toom_evaluate) of `count` operands.
 """
@@ -52,6 +53,8 @@ def main(argv=None):
     ap.add_argument("--limbs", type=int, default=None)
     ap.add_argument("--B", type=int, default=12)
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--method", choices=["newton", "matrix"], default="newton",
+                    help="interp: even-odd Newton route or inverse-Vandermonde matrix")
     args = ap.parse_args(argv)
     import torch
     from . import tc
@@ -88,7 +91,13 @@ def main(argv=None):
         work = torch.empty(max(wb, 1), dtype=torch.uint8, device="cuda")
         torch.cuda.synchronize()
         ctx.close()
-        ms = _time(torch, lambda: tc.tc_toom_interpolate(Y, L, args.B, SU, SV, OUT, work), args.reps)
+        if args.method == "matrix":
+            ms = _time(torch, lambda: tc.tc_toom_interpolate_matrix(Y, L, args.B, SU, SV, OUT),
+                       args.reps)
+        else:
+            ms = _time(torch, lambda: tc.tc_toom_interpolate(Y, L, args.B, SU, SV, OUT, work),
+                       args.reps)
+        res["method"] = args.method
     res.update(count=count, limbs=L, ms_per_call=ms)
     print(json.dumps(res))
 

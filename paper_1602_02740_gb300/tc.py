@@ -79,6 +79,9 @@ _SIGS = {
     "tc_toom_interpolate": (ctypes.c_int, [_sz, _sz, ctypes.c_int, _u32p, _sz, _u8p, _u8p, _u32p,
                                            _sz, _vp, _vp]),
     "tc_toom_interpolate_work_bytes": (ctypes.c_size_t, [_sz, _sz, ctypes.c_int]),
+    "tc_toom_interpolate_matrix": (ctypes.c_int, [_sz, _sz, ctypes.c_int, _u32p, _sz, _u8p, _u8p,
+                                                  _u32p, _sz, _vp]),
+    "tc_interp_matrix_table": (ctypes.c_int, [ctypes.c_int, _i64p, _vp, _vp]),
     "tc_toom_interpolate_noalloc": (ctypes.c_int, [_sz, _sz, ctypes.c_int, _u32p, _sz, _u8p, _u8p,
                                                    _u32p, _sz, _vp]),
     "tc_serve_submit": (ctypes.c_int, [_vp, _u32p, _sz, _u32p, _sz, _u32p,
@@ -393,6 +396,31 @@ def tc_toom_interpolate(Y, limbs: int, B: int, SGN_U=None, SGN_V=None, OUT=None,
                                      _ptr(OUT), OUT.stride(0), _ptr(work) if wb else None,
                                      _stream(stream)), "tc_toom_interpolate")
     return OUT
+
+
+def tc_toom_interpolate_matrix(Y, limbs: int, B: int, SGN_U=None, SGN_V=None, OUT=None,
+                               stream=None):
+    """Interpolation by the inverse Vandermonde matrix (B <= 4, values <= 256 limbs);
+    same layout and result as tc_toom_interpolate."""
+    import torch
+    count = Y.shape[0]
+    if OUT is None:
+        OUT = torch.empty((count, 2 * limbs), dtype=torch.int32, device=Y.device)
+    _check(lib().tc_toom_interpolate_matrix(count, limbs, B, _ptr(Y), Y.shape[-1], _ptr(SGN_U),
+                                            _ptr(SGN_V), _ptr(OUT), OUT.stride(0),
+                                            _stream(stream)), "tc_toom_interpolate_matrix")
+    return OUT
+
+
+def tc_interp_matrix_table(B: int):
+    """Host-side integer form of V^-1 for B blocks: (M[(2B-1), (2B-1)], shift, odd)."""
+    npts = 2 * B - 1
+    M = np.zeros((npts, npts), dtype=np.int64)
+    shift = np.zeros(npts, dtype=np.int32)
+    odd = np.zeros(npts, dtype=np.uint32)
+    _check(lib().tc_interp_matrix_table(B, M.ctypes.data, shift.ctypes.data, odd.ctypes.data),
+           "tc_interp_matrix_table")
+    return M, shift, odd
 
 
 TC_NOALLOC_SCRATCH_BYTES = 16 << 20

@@ -142,6 +142,76 @@ def test_interpolate_vs_oracle(tc, B, L, kind):
         assert same_limbs(out[k], want[k]), (B, L, kind, k)
 
 
+MATRIX_CASES = [(2, 4), (2, 100), (2, 250), (3, 9), (3, 150), (3, 300), (3, 378),
+                (4, 16), (4, 200), (4, 457), (4, 504)]
+
+
+@pytest.mark.parametrize("B,L", MATRIX_CASES)
+@pytest.mark.parametrize("kind", ["uniform", "all_ones", "sparse"])
+def test_interpolate_matrix_vs_oracle(tc, B, L, kind):
+    """Inverse-Vandermonde interpolation (one pass per coefficient) against the
+    oracle's product and the Newton route's output, limb for limb."""
+    import torch
+    count = 3
+    _, e, _, ystride = tc.tc.level_sizes(L, B)
+    Y = np.zeros((count, 2 * B - 1, ystride), dtype=np.uint32)
+    S = np.zeros((count, 2 * B - 1), dtype=np.uint8)
+    want = []
+    for k in range(count):
+        a = inputs.operand(kind, L, 41 * L + k)
+        b = inputs.operand(kind, L, 43 * L + k + 1)
+        y = _oracle_level(to_int(a), to_int(b), L, B)
+        for p, val in enumerate(y):
+            Y[k, p, :2 * e] = from_int(abs(val), 2 * e)
+            S[k, p] = 1 if val < 0 else 0
+        want.append(to_int(a) * to_int(b))
+    dY, dS = dev(Y), torch.from_numpy(S).cuda()
+    out = host(tc.tc.tc_toom_interpolate_matrix(dY, L, B, SGN_U=dS))
+    ref = host(tc.tc.tc_toom_interpolate(dY, L, B, SGN_U=dS))
+    for k in range(count):
+        assert same_limbs(out[k], want[k]), (B, L, kind, k)
+    assert np.array_equal(out, ref)
+
+
+def test_interpolate_matrix_many_products(tc):
+    """The bench's level-2 shape (B = 4, 457-limb operands) over many products and
+    several blocks: equal to the Newton route everywhere, to the oracle on samples."""
+    import torch
+    B, L, count = 4, 457, 3000
+    _, e, _, ystride = tc.tc.level_sizes(L, B)
+    rng = np.random.default_rng(5)
+    Y = np.zeros((count, 2 * B - 1, ystride), dtype=np.uint32)
+    S = np.zeros((count, 2 * B - 1), dtype=np.uint8)
+    want = {}
+    for k in range(count):
+        a = inputs.uniform(L, 7000 + k)
+        b = inputs.uniform(L, 9000 + k)
+        y = _oracle_level(to_int(a), to_int(b), L, B)
+        for p, val in enumerate(y):
+            Y[k, p, :2 * e] = from_int(abs(val), 2 * e)
+            S[k, p] = 1 if val < 0 else 0
+        if k % 500 == 0 or k == count - 1:
+            want[k] = to_int(a) * to_int(b)
+    dY, dS = dev(Y), torch.from_numpy(S).cuda()
+    out = host(tc.tc.tc_toom_interpolate_matrix(dY, L, B, SGN_U=dS))
+    ref = host(tc.tc.tc_toom_interpolate(dY, L, B, SGN_U=dS))
+    assert np.array_equal(out, ref)
+    for k, w in want.items():
+        assert same_limbs(out[k], w), k
+
+
+def test_interpolate_matrix_rejects_unsupported(tc):
+    import torch
+    t = tc.tc
+    Y = torch.zeros((1, 9, 64), dtype=torch.int32, device="cuda")
+    with pytest.raises(t.TCError):
+        t.tc_toom_interpolate_matrix(Y, 100, 5)          # B = 5: not supported
+    _, e, _, ystride = t.level_sizes(2000, 4)
+    Y = torch.zeros((1, 7, ystride), dtype=torch.int32, device="cuda")
+    with pytest.raises(t.TCError):
+        t.tc_toom_interpolate_matrix(Y, 2000, 4)         # values longer than 256 limbs
+
+
 # ---------------------------------------------------------------- whole product
 
 MUL_CASES = [
