@@ -408,6 +408,7 @@ def main():
     e2e = {"value": world * P / e2e_s, "unit": "mults/s",
            "h2d_bytes_per_step": 2 * P * L * 4, "d2h_bytes_per_step": P * 2 * L * 4,
            "api": "tc_pipe_submit x %d + tc_pipe_wait (pinned host buffers)" % e2e_steps,
+           "pinned": bool(hA.is_pinned() and hB.is_pinned() and hO.is_pinned()),
            "blocking": {"api": "tc_mul_uniform_host", "value": world * P / blk_s}}
 
     # ---- B sweep: top-level B in {2,3,4,8,16}; lower levels = the cost model's 3 best ----
