@@ -455,9 +455,9 @@ def main():
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / reps
 
-    configs = None
+    other = None
     if not args.no_configs:
-        configs = {}
+        other = {}
         # one Toom-3 level over a batch of 1024-limb products, and one product alone
         n3 = 16384
         a3 = torch.randint(-2 ** 31, 2 ** 31 - 1, (n3, 1024), dtype=torch.int32, device="cuda")
@@ -466,7 +466,7 @@ def main():
 
         ms_b = timed(lambda: tc.tc_mul_uniform(ctx, a3, b3, o3, plan=[3]), 10)
         ms_1 = timed(lambda: tc.tc_mul(ctx, a3[0], b3[0], o3[0], plan=[3]), 1000)
-        configs["toom3_1024_limbs"] = {"plan": [3], "batch": n3,
+        other["toom3_1024_limbs"] = {"plan": [3], "batch": n3,
                                        "ns_per_product_batched": ms_b * 1e6 / n3,
                                        "ns_per_product_single": ms_1 * 1e6, "reps_single": 1000}
         del a3, b3, o3
@@ -478,7 +478,7 @@ def main():
             dA2 = torch.from_numpy(reps_rows.view(np.int32)).to("cuda")
             ms_k = timed(lambda: tc.tc_mul_uniform(ctx, dA2, dA2 if kind == "all_ones" else dB, dO,
                                                    plan=used_plan), 3)
-            configs[f"{kind}_2e20"] = {"mults_per_s": P / (ms_k / 1e3), "plan": used_plan,
+            other[f"{kind}_2e20"] = {"mults_per_s": P / (ms_k / 1e3), "plan": used_plan,
                                        "operands": "all-ones squared" if kind == "all_ones"
                                        else "sparse (1 % nonzero limbs) x uniform"}
             del dA2
@@ -549,7 +549,7 @@ def main():
                        "limbs": L, "batch_per_gpu": P, "plan": used_plan,
                        "l2": f"operands ({2 * P * L * 4 / 1e6:.0f} MB) exceed the 129 MB L2; no flush"},
             "roofline": roof, "phases": phase_summary, "sweep": sweep,
-            "mixed_batch": mixed, "serving": serve, "configs": configs, "large": large,
+            "mixed_batch": mixed, "serving": serve, "configs": other, "large": large,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
         }
         print(json.dumps(line), flush=True)
