@@ -178,7 +178,9 @@ tc_status tc_mul_uniform_host(tc_ctx *ctx, size_t count, size_t limbs,
  * semantics) or products.  tc_pipe_wait blocks until every submitted batch is
  * complete.  Errors: TC_EINVAL (null or zero arguments, a context of another
  * device), TC_ENOMEM (the pipe's memory exceeds the context's budget),
- * TC_EDEVICE.  tc_pipe_destroy waits for the pipe and frees it (NULL ignored).
+ * TC_EDEVICE; after an error from tc_pipe_submit or tc_pipe_wait the pipe's
+ * state is undefined: destroy it.  tc_pipe_destroy waits for the pipe and
+ * frees it (NULL ignored).
  */
 typedef struct tc_pipe tc_pipe;
 tc_status tc_pipe_create(tc_ctx *ctx, size_t count, size_t limbs, int square,
