@@ -22,12 +22,13 @@ import time
 BS = (2, 3, 4, 5, 6, 8, 12, 16, 32)
 LEAF_MIN, LEAF_MAX = 24, 224
 
-# cost-model rates (per second), rough figures measured on GB300 with the current
-# kernels (2^20-bit batch: base case 5.5 T limb products/s; interpolation
-# 2.3-2.9e11 n^2 Y products-limbs/s; evaluation 4-11e11 B n e rows-limbs/s)
-LEAF_RATE = 5.5e12        # base-case limb products
-INTERP_RATE = 2.7e11      # n^2 x interpolation-value limbs
-EVAL_RATE = 6.0e11        # B x n x evaluation limbs
+# cost-model rates (per second), measured on GB300 with the current kernels on
+# the 2^20-bit batch (2432 products, plan [12, 6, 4]): base case 6.9 T limb
+# products/s; interpolation 3.1-4.3e11 n^2 Y product-limbs/s (levels 0, 1, 2:
+# 3.4, 3.1, 4.3e11); evaluation 1.0-1.5e12 B n e row-limbs/s (1.4, 1.5, 1.0e12)
+LEAF_RATE = 6.9e12        # base-case limb products
+INTERP_RATE = 3.5e11      # n^2 x interpolation-value limbs
+EVAL_RATE = 1.3e12        # B x n x evaluation limbs
 LAUNCH_S = 6e-6           # per kernel launch
 
 
