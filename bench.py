@@ -42,13 +42,6 @@ SM_COUNT = 152
 IMAD_PER_CLK_SM = 64     # 32-bit integer multiply(-add) results per clock per SM
 IMAD_PER_LIMB_PRODUCT = 2  # low and high halves of a 32 x 32 -> 64-bit product
 
-# DRAM traffic of the base-case kernel from one ncu capture (profiles/leaf_pair_2e20.md):
-# leaf_pair_kernel<false> on 269192 products of 116 limbs moved 4.5072e8 bytes
-# (dram__bytes_read.sum + dram__bytes_write.sum); traffic grows with the number
-# of products, so a launch of N such products moves N * 1674 bytes.
-LEAF_TRAFFIC = {"kernel": "leaf_pair_kernel<false>", "limbs": 116, "bytes_per_product": 4.50208256e8 / 269192}
-
-
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -68,6 +61,13 @@ def parse():
                    help="skip the Toom-3 at 1024 limbs and the all-ones / sparse 2^20-bit lines")
     p.add_argument("--large", action="store_true",
                    help="also time single products of 2^24, 2^26 and 2^27 bits (and squares)")
+    p.add_argument("--case", choices=["interp", "leaf", "eval"], default=None,
+                   help="time one kernel call for a profiler capture instead of the benchmark")
+    p.add_argument("--count", type=int, default=None, help="--case: products or rows")
+    p.add_argument("--B", type=int, default=12, help="--case interp/eval: blocks")
+    p.add_argument("--reps", type=int, default=3, help="--case: timed repetitions")
+    p.add_argument("--method", choices=["newton", "matrix"], default="newton",
+                   help="--case interp: even-odd Newton route or inverse-Vandermonde matrix")
     return p.parse_args()
 
 
@@ -314,6 +314,87 @@ def rank_seed(rank: int, k: int) -> int:
     return 1_000_000 * rank + k
 
 
+# ----------------------------------------------------------------- single-kernel cases
+
+def _rand_dev(torch, shape, seed):
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    return torch.randint(-2 ** 31, 2 ** 31 - 1, shape, dtype=torch.int32, device="cuda", generator=g)
+
+
+def _time_case(torch, fn, reps):
+    # the calls under study run inside the NVTX range "measure", so a capture can
+    # select them with: ncu --nvtx --nvtx-include "measure/" ...
+    torch.cuda.nvtx.range_push("measure")
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    return e0.elapsed_time(e1) / reps
+
+
+def run_case(args):
+    """One library call under study (for ncu captures and kernel timing).
+
+    interp: one Toom level's interpolation (tc_toom_interpolate, or with
+            --method matrix tc_toom_interpolate_matrix) of `count` products of
+            `limbs`-limb operands split into B blocks; its inputs are the true
+            pointwise products (evaluation, then products of the evaluations).
+    leaf:   the batched schoolbook (tc_schoolbook) of `count` products.
+    eval:   one level's evaluation (tc_toom_evaluate) of `count` operands.
+    Prints one JSON line with the mean time of `reps` calls after one untimed call.
+    """
+    import torch
+    from paper_1602_02740_gb300 import tc
+    torch.cuda.set_device(0)
+    res = {"case": args.case, "B": args.B, "reps": args.reps}
+    if args.case == "leaf":
+        count, L = args.count or 157320, args.limbs if args.limbs != LIMBS else 184
+        A, B = _rand_dev(torch, (count, L), 1), _rand_dev(torch, (count, L), 2)
+        OUT = torch.empty((count, 2 * L), dtype=torch.int32, device="cuda")
+        ms = _time_case(torch, lambda: tc.tc_schoolbook(A, B, OUT), args.reps)
+    elif args.case == "eval":
+        count, L = args.count or 2432, args.limbs
+        U = _rand_dev(torch, (count, L), 1)
+        _, e, estride, _ = tc.level_sizes(L, args.B)
+        E = torch.empty((count, 2 * args.B - 1, estride), dtype=torch.int32, device="cuda")
+        S = torch.empty((count, 2 * args.B - 1), dtype=torch.uint8, device="cuda")
+        ms = _time_case(torch, lambda: tc.tc_toom_evaluate(U, args.B, E, S), args.reps)
+    else:
+        count, L = args.count or 2048, args.limbs
+        npts = 2 * args.B - 1
+        _, e, estride, ystride = tc.level_sizes(L, args.B)
+        ctx = tc.tc_create(0)
+        U, V = _rand_dev(torch, (count, L), 1), _rand_dev(torch, (count, L), 2)
+        EU, SU = tc.tc_toom_evaluate(U, args.B)
+        EV, SV = tc.tc_toom_evaluate(V, args.B)
+        del U, V
+        Y = torch.zeros((count, npts, ystride), dtype=torch.int32, device="cuda")
+        rows = count * npts
+        tc.tc_mul_uniform(ctx, EU.view(rows, estride)[:, :e], EV.view(rows, estride)[:, :e],
+                          Y.view(rows, ystride)[:, :2 * e])
+        del EU, EV
+        OUT = torch.empty((count, 2 * L), dtype=torch.int32, device="cuda")
+        wb = tc.tc_toom_interpolate_work_bytes(count, L, args.B)
+        work = torch.empty(max(wb, 1), dtype=torch.uint8, device="cuda")
+        torch.cuda.synchronize()
+        ctx.close()
+        if args.method == "matrix":
+            ms = _time_case(torch, lambda: tc.tc_toom_interpolate_matrix(Y, L, args.B, SU, SV, OUT),
+                            args.reps)
+        else:
+            ms = _time_case(torch, lambda: tc.tc_toom_interpolate(Y, L, args.B, SU, SV, OUT, work),
+                            args.reps)
+        res["method"] = args.method
+    res.update(count=count, limbs=L, ms_per_call=ms)
+    print(json.dumps(res), flush=True)
+
+
 # ----------------------------------------------------------------- GPU leg
 
 def main():
@@ -323,6 +404,8 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.case:
+        return run_case(args)
 
     import torch
     from paper_1602_02740_gb300 import inputs, tc

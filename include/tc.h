@@ -93,7 +93,8 @@ tc_status tc_scratch_bytes(tc_ctx *ctx, size_t count, size_t limbs, const tc_opt
  * Unbalanced operands: the shorter operand is zero-padded when the ratio is
  * below 2; otherwise the longer one is cut into pieces of the shorter's
  * length, the pieces are multiplied as one balanced batch, and the partial
- * products are added at their offsets.
+ * products are added at their offsets.  na and nb at most 2^30 limbs, else
+ * TC_EINVAL.
  */
 tc_status tc_mul(tc_ctx *ctx, const uint32_t *a, size_t na, const uint32_t *b, size_t nb,
                  uint32_t *out, const tc_opts *opts, void *stream);
@@ -109,6 +110,8 @@ tc_status tc_sqr(tc_ctx *ctx, const uint32_t *a, size_t na, uint32_t *out,
  * Bv[b_off[k] .. +b_len[k]) and writes OUT[out_off[k] .. +a_len[k]+b_len[k]).
  * Products are grouped into size classes; each class runs level by level
  * (breadth first) with every product of the class in the same launches.
+ * TC_EINVAL (before any launch) if an offset is negative or above 2^40, or a
+ * length is negative or above 2^28 limbs.
  */
 tc_status tc_mul_batch(tc_ctx *ctx, size_t count,
                        const uint32_t *A, const int64_t *a_off, const int64_t *a_len,
@@ -300,7 +303,10 @@ tc_status tc_serve_submit(tc_ctx *ctx, const uint32_t *a, size_t na, const uint3
                           size_t nb, uint32_t *out, uint64_t *ticket);
 
 /* TC_OK when the ticket's product is complete in `out`, TC_EPENDING while it
- * runs, or an error status.  A completed ticket may be polled once more. */
+ * runs, or the request's error status.  The call that reports a final state
+ * (TC_OK or an error) releases the ticket: polling it again returns TC_EINVAL.
+ * tc_serve_stop may run concurrently with tc_serve_submit, tc_serve_poll and
+ * tc_serve_stats (after a stop they see no server: TC_EINVAL for poll). */
 tc_status tc_serve_poll(tc_ctx *ctx, uint64_t ticket);
 
 /* Latency percentiles (submit -> completion seen by the loop) and sustained

@@ -550,7 +550,23 @@ size_t tc::size_class(size_t L) {
     return c;
 }
 
-// Products listed by (offset, length) triples; all device limb buffers, host index arrays.
+// Host index arrays of a packed batch: every offset >= 0 and below 2^40 limbs,
+// every length in [0, 2^28] limbs (the serving limit), checked before any launch
+// so that no gather or scatter is given an address outside the caller's buffers'
+// possible range.
+static bool batch_tables_valid(size_t count, const int64_t* a_off, const int64_t* a_len,
+                               const int64_t* b_off, const int64_t* b_len, const int64_t* out_off) {
+    const int64_t kMaxLen = (int64_t)1 << 28, kMaxOff = (int64_t)1 << 40;
+    for (size_t k = 0; k < count; ++k) {
+        if (a_len[k] < 0 || b_len[k] < 0 || a_len[k] > kMaxLen || b_len[k] > kMaxLen) return false;
+        if (a_off[k] < 0 || b_off[k] < 0 || out_off[k] < 0) return false;
+        if (a_off[k] > kMaxOff || b_off[k] > kMaxOff || out_off[k] > kMaxOff) return false;
+    }
+    return true;
+}
+
+// Products listed by (offset, length) triples; all device limb buffers, host index arrays
+// (validated by batch_tables_valid).
 static tc_status mul_general(tc_ctx* ctx, size_t count, const u32* A, const int64_t* a_off,
                              const int64_t* a_len, const u32* Bm, const int64_t* b_off,
                              const int64_t* b_len, u32* OUT, const int64_t* out_off,
@@ -560,7 +576,6 @@ static tc_status mul_general(tc_ctx* ctx, size_t count, const u32* A, const int6
     std::vector<Item> items;
     items.reserve(count);
     for (size_t k = 0; k < count; ++k) {
-        if (a_len[k] < 0 || b_len[k] < 0) return TC_EINVAL;
         const size_t L = (size_t)std::max(a_len[k], b_len[k]);
         if (a_len[k] == 0 || b_len[k] == 0) {
             const size_t n = (size_t)(a_len[k] + b_len[k]);
@@ -644,6 +659,7 @@ extern "C" tc_status tc_mul_batch(tc_ctx* ctx, size_t count, const uint32_t* A, 
     if (!ctx) return TC_EINVAL;
     if (count == 0) return TC_OK;
     if (!A || !Bv || !OUT || !a_off || !a_len || !b_off || !b_len || !out_off) return TC_EINVAL;
+    if (!batch_tables_valid(count, a_off, a_len, b_off, b_len, out_off)) return TC_EINVAL;
     CK(cudaSetDevice(ctx->device));
     return mul_general(ctx, count, A, a_off, a_len, Bv, b_off, b_len, OUT, out_off, opts,
                        (cudaStream_t)stream);
@@ -680,14 +696,13 @@ extern "C" tc_status tc_batch_prepare(tc_ctx* ctx, size_t count, const int64_t* 
                                       const tc_opts* opts, tc_batch** out) {
     if (!ctx || !out || (count && (!a_off || !a_len || !b_off || !b_len || !out_off))) return TC_EINVAL;
     *out = nullptr;
+    if (!batch_tables_valid(count, a_off, a_len, b_off, b_len, out_off)) return TC_EINVAL;
     CK(cudaSetDevice(ctx->device));
     std::unique_ptr<tc_batch> bt(new tc_batch);
     bt->device = ctx->device;
     struct Item { size_t k, cls; };
     std::vector<Item> items;
     for (size_t k = 0; k < count; ++k) {
-        if (a_len[k] < 0 || b_len[k] < 0 || a_off[k] < 0 || b_off[k] < 0 || out_off[k] < 0)
-            return TC_EINVAL;
         if (a_len[k] == 0 || b_len[k] == 0) {
             if (a_len[k] + b_len[k]) bt->zeros.push_back({out_off[k], a_len[k] + b_len[k]});
             continue;
@@ -823,6 +838,7 @@ extern "C" void tc_batch_destroy(tc_batch* bt) {
 extern "C" tc_status tc_mul(tc_ctx* ctx, const uint32_t* a, size_t na, const uint32_t* b, size_t nb,
                             uint32_t* out, const tc_opts* opts, void* stream) {
     if (!ctx || !out || (na && !a) || (nb && !b)) return TC_EINVAL;
+    if (na > ((size_t)1 << 30) || nb > ((size_t)1 << 30)) return TC_EINVAL;
     CK(cudaSetDevice(ctx->device));
     cudaStream_t st = (cudaStream_t)stream;
     if (na == 0 || nb == 0) {

@@ -25,21 +25,26 @@ namespace {
 __device__ __align__(256) unsigned char noalloc_scratch[TC_NOALLOC_SCRATCH_BYTES];
 
 constexpr int MAX_DEVICES = 64;
-std::once_flag g_once[MAX_DEVICES];
+std::mutex g_mu[MAX_DEVICES];
 void* g_addr[MAX_DEVICES];
-cudaError_t g_err[MAX_DEVICES];
 
-// Device address of noalloc_scratch on the current device (looked up on the
-// first call per device; later calls reuse it).
+// Device address of noalloc_scratch on the current device.  A successful
+// lookup is cached for the device; a failed one is returned and not cached, so
+// the next call tries again.
 cudaError_t scratch_address(int device, void** out) {
-    std::call_once(g_once[device], [device]() {
+    std::lock_guard<std::mutex> lk(g_mu[device]);
+    if (!g_addr[device]) {
         void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, noalloc_scratch);
-        g_addr[device] = e == cudaSuccess ? p : nullptr;
-        g_err[device] = e;
-    });
+        const cudaError_t e = cudaGetSymbolAddress(&p, noalloc_scratch);
+        if (e != cudaSuccess) {
+            cudaGetLastError();  // clear it: the next call starts clean
+            *out = nullptr;
+            return e;
+        }
+        g_addr[device] = p;
+    }
     *out = g_addr[device];
-    return g_err[device];
+    return cudaSuccess;
 }
 
 }  // namespace

@@ -236,8 +236,8 @@ void Server::run() {
 
 static std::mutex g_server_mu;
 
-static Server* get_server(tc_ctx* ctx, tc_status* st) {
-    std::lock_guard<std::mutex> lk(g_server_mu);
+// The context's server, started on first use.  The caller holds g_server_mu.
+static Server* get_server_locked(tc_ctx* ctx, tc_status* st) {
     *st = TC_OK;
     if (ctx->server) return ctx->server;
     Server* s = new Server();
@@ -284,10 +284,16 @@ extern "C" tc_status tc_serve_submit(tc_ctx* ctx, const uint32_t* a, size_t na, 
     const size_t need = cls ? group_bytes(ctx, 1, cls) : 0;
     if (need > ctx->budget) return TC_ENOMEM;  // could never be admitted
     tc_status st;
-    Server* s = get_server(ctx, &st);
-    if (!s) return st;
     Request* r = new Request{0, a, na, b, nb, out, cls, need, now_s(), 0};
+    Server* s = nullptr;
     {
+        // g_server_mu held throughout: tc_serve_stop cannot detach the server meanwhile
+        std::lock_guard<std::mutex> glk(g_server_mu);
+        s = get_server_locked(ctx, &st);
+        if (!s) {
+            delete r;
+            return st;
+        }
         std::lock_guard<std::mutex> lk(s->mu);
         if (s->stopping || s->slots_used >= Server::kMaxSlots || s->reserved + need > s->budget) {
             delete r;
@@ -299,22 +305,29 @@ extern "C" tc_status tc_serve_submit(tc_ctx* ctx, const uint32_t* a, size_t na, 
         if (s->first_submit < 0) s->first_submit = r->t_submit;
         s->queue.push_back(r);
         s->all[r->ticket] = r;
+        *ticket = r->ticket;  // r may be released by a poll once the locks are dropped
+        s->cv.notify_one();
     }
-    s->cv.notify_one();
-    *ticket = r->ticket;
     return TC_OK;
 }
 
+// The server is read under g_server_mu, which tc_serve_stop holds while it
+// detaches the server, so a poll never sees a server that is being deleted.
+// A final state (done or an error) releases the ticket: the worker no longer
+// refers to a request once its state is final.
 extern "C" tc_status tc_serve_poll(tc_ctx* ctx, uint64_t ticket) {
-    if (!ctx || !ctx->server) return TC_EINVAL;
+    if (!ctx) return TC_EINVAL;
+    std::lock_guard<std::mutex> glk(g_server_mu);
     Server* s = ctx->server;
+    if (!s) return TC_EINVAL;
     std::lock_guard<std::mutex> lk(s->mu);
     auto it = s->all.find(ticket);
     if (it == s->all.end()) return TC_EINVAL;
     const int state = it->second->state;
-    if (state == 2) return TC_OK;
-    if (state < 0) return (tc_status)state;
-    return TC_EPENDING;
+    if (state == 1 || state == 0) return TC_EPENDING;
+    delete it->second;
+    s->all.erase(it);
+    return state == 2 ? TC_OK : (tc_status)state;
 }
 
 extern "C" tc_status tc_serve_stats(tc_ctx* ctx, double* p50_ms, double* p99_ms, double* bits_per_s,
@@ -322,17 +335,19 @@ extern "C" tc_status tc_serve_stats(tc_ctx* ctx, double* p50_ms, double* p99_ms,
     if (!ctx) return TC_EINVAL;
     double p50 = 0, p99 = 0, bps = 0;
     uint64_t n = 0;
-    if (ctx->server) {
-        Server* s = ctx->server;
-        std::vector<double> lat;
-        double bits, t0, t1;
-        {
+    std::vector<double> lat;
+    double bits = 0, t0 = 0, t1 = 0;
+    {
+        std::lock_guard<std::mutex> glk(g_server_mu);  // see tc_serve_poll
+        if (Server* s = ctx->server) {
             std::lock_guard<std::mutex> lk(s->mu);
             lat = s->lat_ms;
             bits = s->bits;
             t0 = s->first_submit;
             t1 = s->last_done;
         }
+    }
+    {
         n = lat.size();
         if (n) {
             std::sort(lat.begin(), lat.end());

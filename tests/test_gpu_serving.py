@@ -101,3 +101,22 @@ def test_admission_by_budget(tc):
         assert busy > 0   # the 64 MB budget cannot hold 400 of these at once
     finally:
         ctx.close()
+
+
+def test_ticket_released_after_final_poll(tc):
+    t = tc.tc
+    ctx = t.tc_create(0, budget_bytes=1 << 30)
+    try:
+        a = t.to_device(inputs.uniform(500, 3))
+        b = t.to_device(inputs.uniform(500, 4))
+        import torch
+        out = torch.empty(1000, dtype=torch.int32, device="cuda")
+        k = t.tc_serve_submit(ctx, a, b, out)
+        assert k >= 0
+        _wait_all(t, ctx, [k])
+        with pytest.raises(t.TCError) as ei:   # the final poll released the ticket
+            t.tc_serve_poll(ctx, k)
+        assert ei.value.status == t.TC_EINVAL
+        assert to_int(t.to_numpy(out)) == to_int(t.to_numpy(a)) * to_int(t.to_numpy(b))
+    finally:
+        ctx.close()

@@ -73,3 +73,29 @@ def test_host_argument_checks_without_gpu(libtc):
     libtc.tc_pipe_destroy(None)
     libtc.tc_batch_destroy.argtypes = [vp]
     libtc.tc_batch_destroy(None)
+
+
+def test_batch_tables_rejected_on_the_host(libtc):
+    """Negative or huge offsets and lengths in a packed batch are rejected
+    (TC_EINVAL) before the context is used or anything is launched."""
+    import numpy as np
+    vp = ctypes.c_void_p
+    libtc.tc_mul_batch.argtypes = [vp, ctypes.c_size_t, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+    libtc.tc_batch_prepare.argtypes = [vp, ctypes.c_size_t, vp, vp, vp, vp, vp, vp,
+                                       ctypes.POINTER(vp)]
+    fake_ctx = ctypes.create_string_buffer(64)     # never dereferenced: rejected first
+    fake_buf = ctypes.create_string_buffer(64)
+    good = dict(a_off=[0, 8], a_len=[4, 4], b_off=[0, 8], b_len=[4, 4], o_off=[0, 16])
+    for key, bad in (("a_off", -1), ("b_off", -5), ("o_off", -8), ("a_len", -1),
+                     ("b_len", -2), ("a_len", (1 << 28) + 1), ("a_off", (1 << 40) + 1)):
+        arrs = {k: np.array(v, dtype=np.int64) for k, v in good.items()}
+        arrs[key][1] = bad
+        p = {k: arrs[k].ctypes.data_as(vp) for k in arrs}
+        st = libtc.tc_mul_batch(ctypes.addressof(fake_ctx), 2, ctypes.addressof(fake_buf),
+                                p["a_off"], p["a_len"], ctypes.addressof(fake_buf), p["b_off"],
+                                p["b_len"], ctypes.addressof(fake_buf), p["o_off"], None, None)
+        assert st == -1, (key, bad)
+        h = vp()
+        st = libtc.tc_batch_prepare(ctypes.addressof(fake_ctx), 2, p["a_off"], p["a_len"],
+                                    p["b_off"], p["b_len"], p["o_off"], None, ctypes.byref(h))
+        assert st == -1 and not h.value, (key, bad)

@@ -44,7 +44,12 @@ CASES = [(16, 32768, 2), (8, 20000, 3), (4, 300, 5)]
 def test_noalloc_matches_regular_entry_point_twice(tc, B, L, count):
     import torch
     t = tc.tc
-    assert t.tc_toom_interpolate_work_bytes(count, L, B) <= t.TC_NOALLOC_SCRATCH_BYTES
+    wb = t.tc_toom_interpolate_work_bytes(count, L, B)
+    assert wb <= t.TC_NOALLOC_SCRATCH_BYTES
+    if L > 300:
+        assert wb > 0, "this case is meant to run through the built-in scratch"
+    else:
+        assert wb == 0
     Y, S = _level_inputs(t, B, L, count, seed=100 * B + L)
     want = t.to_numpy(t.tc_toom_interpolate(Y, L, B, SGN_U=S))
     for call in range(2):  # two calls in a row share the built-in scratch
