@@ -502,18 +502,31 @@ def test_interpolate_many_products(tc, B, L):
         assert same_limbs(out[k], to_int(A[k]) * to_int(Bm[k])), (B, L, k)
 
 
-def test_uniform_batch_bench_launch(ctx, tc):
+def test_uniform_batch_bench_launch(tc):
     """The timed workload in its own launch configuration: 2432 products of
-    2^20-bit operands in one call, plan [12, 5, 3] (levels of 2432, 55 936 and
-    503 424 products; 2 522 880 base-case products of 184 limbs).  Every
-    product is checked modulo three 61-bit primes, sampled ones exactly."""
+    2^20-bit operands in one tc_mul_uniform call, with the plan the benchmark
+    takes from the plan table ([12, 6, 4]: levels of 2432, 55 936 and 615 296
+    products, 4 307 072 base-case products of 116 limbs; the streaming
+    interpolation at n = 11 and n = 5, the register-resident one at n = 3 and
+    the pair base case).  Every product is checked modulo three 61-bit primes,
+    sampled ones limb by limb; rows 5 and 6 are all-ones and sparse."""
+    import os
+    t = tc.tc
     L, count = 32768, 2432
-    A = np.stack([inputs.uniform(L, 1000 + 2 * k) for k in range(count)])
-    B = np.stack([inputs.uniform(L, 1001 + 2 * k) for k in range(count)])
-    A[5] = 0xFFFFFFFF
-    B[5] = 0xFFFFFFFF
-    OUT = host(tc.tc.tc_mul_uniform(ctx, dev(A), dev(B), plan=[12, 5, 3]))
-    for k in (0, 5, 1217, count - 1):
+    table = os.path.join(os.path.dirname(tc.__file__), "plans_gb300.txt")
+    ctx = t.tc_create(0, table=table)
+    try:
+        plan = t.tc_plan_for(ctx, L)
+        assert plan == [12, 6, 4], plan     # the plan the benchmark line reports
+        A = np.stack([inputs.uniform(L, 1000 + 2 * k) for k in range(count)])
+        B = np.stack([inputs.uniform(L, 1001 + 2 * k) for k in range(count)])
+        A[5] = 0xFFFFFFFF
+        B[5] = 0xFFFFFFFF
+        A[6] = inputs.sparse(L, 77)
+        OUT = host(t.tc_mul_uniform(ctx, dev(A), dev(B), plan=plan))
+    finally:
+        ctx.close()
+    for k in (0, 5, 6, 1217, count - 1):
         assert same_limbs(OUT[k], to_int(A[k]) * to_int(B[k])), k
     for k in range(count):
         assert residues.product_residues_match(A[k], B[k], OUT[k]), k
