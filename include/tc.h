@@ -333,6 +333,7 @@ typedef struct {
     double ms;             /* summed event time */
     double bytes;          /* summed algorithmic bytes */
     double limb_products;  /* summed limb products (base case only) */
+    char kernel[48];       /* name of the kernel (or kernel sequence) the step launched */
 } tc_phase_stat;
 
 /* Turn phase timing on (1) or off (0); turning it on clears the records. */
@@ -341,6 +342,19 @@ tc_status tc_profile_enable(tc_ctx *ctx, int on);
 /* Wait for the recorded events and report up to `cap` phases in *out
  * (one entry per kind and level); *n receives the number written. */
 tc_status tc_profile_read(tc_ctx *ctx, tc_phase_stat *out, int cap, int *n);
+
+/*
+ * Integer ceiling of the base case (a measurement kernel; the paper has no
+ * counterpart).  Enqueues on `stream` `blocks` CTAs of 256 threads, each
+ * thread running `iters` iterations of 64 register-only limb products, each
+ * added into a 96-bit column sum by the base case's own instruction sequence
+ * (mad.lo.cc, madc.hi.cc, addc).  *limb_products receives the number of limb
+ * products the launch performs; time the launch with events on `stream` to
+ * get limb products per second.  `sink` is a device buffer of blocks * 256
+ * uint32 (one checksum per thread, so the work cannot be elided).  TC_EINVAL
+ * for non-positive sizes or null pointers.
+ */
+tc_status tc_peak_madc(int blocks, int iters, uint32_t *sink, void *stream, double *limb_products);
 
 /* Message for a status code (static string). */
 const char *tc_strerror(tc_status s);

@@ -158,7 +158,7 @@ struct PhaseTimer {
         if (!ctx || !ctx->profile || !a) return;
         cudaEvent_t b = get(ctx);
         cudaEventRecord(b, st);
-        ctx->recs.push_back({kind, level, a, b, bytes, lp});
+        ctx->recs.push_back({kind, level, a, b, bytes, lp, g_kernel_name});
         a = nullptr;
     }
 };
@@ -964,7 +964,12 @@ extern "C" tc_status tc_profile_read(tc_ctx* ctx, tc_phase_stat* out, int cap, i
         for (auto& x : acc)
             if (x.kind == r.kind && x.level == r.level) p = &x;
         if (!p) {
-            acc.push_back({r.kind, r.level, 0, 0.0, 0.0, 0.0});
+            tc_phase_stat x;
+            memset(&x, 0, sizeof x);
+            x.kind = r.kind;
+            x.level = r.level;
+            snprintf(x.kernel, sizeof x.kernel, "%s", r.kernel ? r.kernel : "");
+            acc.push_back(x);
             p = &acc.back();
         }
         p->launches += 1;

@@ -361,6 +361,7 @@ cudaError_t launch_schoolbook_big(const u32* A, long lda, const u32* Bm, long ld
                                   long ldo, int s, long P, u32* cols, cudaStream_t st) {
     if (P <= 0) return cudaSuccess;
     const int ctiles = (2 * s + BIG_COLS - 1) / BIG_COLS;
+    note_kernel("bigmul_columns_kernel+bigmul_normalise_kernel");
     bigmul_columns_kernel<<<(unsigned)(P * ctiles), BIG_COLS / 4, 0, st>>>(A, lda, Bm, ldb, cols, s, ctiles);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -667,17 +668,23 @@ cudaError_t launch_leaf(const u32* A, long lda, const u32* Bm, long ldb, u32* OU
             });
             const unsigned grid = (unsigned)((P + 16 * PAIR_WARPS - 1) / (16 * PAIR_WARPS));
             const size_t smem = per_warp * PAIR_WARPS;
-            if (square)
+            if (square) {
+                note_kernel("leaf_pair_kernel<true>");
                 leaf_pair_kernel<true><<<grid, 32 * PAIR_WARPS, smem, st>>>(A, lda, Bm, ldb, OUT, ldo, s, P, vec);
-            else
+            } else {
+                note_kernel("leaf_pair_kernel<false>");
                 leaf_pair_kernel<false><<<grid, 32 * PAIR_WARPS, smem, st>>>(A, lda, Bm, ldb, OUT, ldo, s, P, vec);
+            }
             return cudaGetLastError();
         }
         const unsigned grid = (unsigned)((P + 127) / 128);
-        if (square)
+        if (square) {
+            note_kernel("leaf_lane_kernel<true>");
             leaf_lane_kernel<true><<<grid, 128, 0, st>>>(A, lda, Bm, ldb, OUT, ldo, s, P, vec);
-        else
+        } else {
+            note_kernel("leaf_lane_kernel<false>");
             leaf_lane_kernel<false><<<grid, 128, 0, st>>>(A, lda, Bm, ldb, OUT, ldo, s, P, vec);
+        }
         return cudaGetLastError();
     }
     LeafGeom g = leaf_geom(s);
@@ -694,6 +701,7 @@ cudaError_t launch_leaf(const u32* A, long lda, const u32* Bm, long ldb, u32* OU
         cudaFuncSetAttribute(leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
     });
     const long grid = (P + ppc - 1) / ppc;
+    note_kernel("leaf_kernel");
     leaf_kernel<<<(unsigned)grid, threads, smem, st>>>(A, lda, Bm, ldb, OUT, ldo, g, P, ppc);
     return cudaGetLastError();
 }

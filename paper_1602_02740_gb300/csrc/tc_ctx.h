@@ -48,7 +48,7 @@ struct tc_ctx {
     tc::Server* server = nullptr;
     // phase timing (tc_profile_enable)
     bool profile = false;
-    struct Rec { int kind, level; cudaEvent_t a, b; double bytes, lp; };
+    struct Rec { int kind, level; cudaEvent_t a, b; double bytes, lp; const char* kernel; };
     std::vector<Rec> recs;
     std::vector<cudaEvent_t> event_pool;
 };

@@ -6,6 +6,11 @@
 
 namespace tc {
 
+// Name of the kernel (or kernel sequence) the last launch_* call on this thread
+// chose; the phase timer records it beside each launch's time.
+extern thread_local const char* g_kernel_name;
+inline void note_kernel(const char* name) { g_kernel_name = name; }
+
 // Geometry of one Toom level for operands of s limbs split into B blocks.
 struct LevelGeom {
     int B, n;      // blocks, degree n = B - 1

@@ -16,6 +16,8 @@
 
 namespace tc {
 
+thread_local const char* g_kernel_name = "";
+
 LevelGeom make_level(int s, int B) {
     LevelGeom g;
     g.B = B;
@@ -480,13 +482,14 @@ cudaError_t launch_eval(const u32* in, long in_stride, const LevelGeom& g, u32* 
             const size_t smem = (size_t)wpb * rowlen * 4;
             switch (g.B) {
 #define TC_EVAL_PTS(BB) \
-    case BB: eval_pts_kernel<BB><<<(unsigned)grid, wpb * 32, smem, st>>>(in, in_stride, g, out, sgn, P, rowlen); \
+    case BB: note_kernel("eval_pts_kernel<" #BB ">"); eval_pts_kernel<BB><<<(unsigned)grid, wpb * 32, smem, st>>>(in, in_stride, g, out, sgn, P, rowlen); \
         return cudaGetLastError();
                 TC_EVAL_PTS(2) TC_EVAL_PTS(3) TC_EVAL_PTS(4) TC_EVAL_PTS(5)
                 TC_EVAL_PTS(6) TC_EVAL_PTS(7) TC_EVAL_PTS(8)
 #undef TC_EVAL_PTS
                 default: break;
             }
+            note_kernel("eval_warp_kernel");
             eval_warp_kernel<<<(unsigned)grid, wpb * 32, (size_t)wpb * rowlen * 4, st>>>(
                 in, in_stride, g, out, sgn, P, rowlen);
             return cudaGetLastError();
@@ -495,10 +498,13 @@ cudaError_t launch_eval(const u32* in, long in_stride, const LevelGeom& g, u32* 
     const int warps = g.n < 1 ? 1 : g.n;  // n <= 31: one warp per point pair
     const int W = ((g.n - 1) * g.n >> 5) + 1;
     const size_t smem = (size_t)2 * g.B * ((CH + W) + ((CH + W) >> 5) + 1) * 4;  // two chunk buffers
-    if (warps * 32 <= 384)  // up to B = 13: three blocks per SM (at most 56 registers)
+    if (warps * 32 <= 384) {  // up to B = 13: three blocks per SM (at most 56 registers)
+        note_kernel("eval_kernel<384,3>");
         eval_kernel<384, 3><<<(unsigned)P, warps * 32, smem, st>>>(in, in_stride, g, out, sgn, P);
-    else
+    } else {
+        note_kernel("eval_kernel<1024,1>");
         eval_kernel<1024, 1><<<(unsigned)P, warps * 32, smem, st>>>(in, in_stride, g, out, sgn, P);
+    }
     return cudaGetLastError();
 }
 
@@ -1665,6 +1671,7 @@ static cudaError_t launch_reg_interp(const InterpArgs& a, long P, cudaStream_t s
                              200 * 1024);
     });
     const long grid = (P + wpb - 1) / wpb;
+    note_kernel(KL == 8 ? "interp_reg_kernel<8>" : KL == 12 ? "interp_reg_kernel<12>" : "interp_reg_kernel<16>");
     interp_reg_kernel<KL, N><<<(unsigned)grid, wpb * 32, wpb * per_warp, st>>>(a, dtk, P);
     return cudaGetLastError();
 }
@@ -1763,6 +1770,7 @@ cudaError_t launch_interp(const LevelGeom& g, const u32* y, const uint8_t* su, c
                                      STREAM_SMEM_MAX);
             });
             const long grid = (P + best_w - 1) / best_w;
+            note_kernel("interp_stream_kernel");
             interp_stream_kernel<<<(unsigned)grid, best_w * 32, (size_t)best_w * per_warp, st>>>(a, dt, ft, P);
             return cudaGetLastError();
         }
@@ -1775,6 +1783,7 @@ cudaError_t launch_interp(const LevelGeom& g, const u32* y, const uint8_t* su, c
                                  200 * 1024);
         });
         const long grid = (P + wpb - 1) / wpb;
+        note_kernel("interp_warp_kernel");
         interp_warp_kernel<<<(unsigned)grid, wpb * 32, a.use_smem ? wpb * warp_smem : 0, st>>>(a, dt, P);
         return cudaGetLastError();
     }
@@ -1799,10 +1808,13 @@ cudaError_t launch_interp(const LevelGeom& g, const u32* y, const uint8_t* su, c
         cudaFuncSetAttribute(interp_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
         cudaFuncSetAttribute(interp_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
     });
-    if (g.K == 8)
+    if (g.K == 8) {
+        note_kernel("interp_kernel<8>");
         interp_kernel<8><<<(unsigned)P, warps * 32, smem, st>>>(a, dt8, P);
-    else
+    } else {
+        note_kernel("interp_kernel<4>");
         interp_kernel<4><<<(unsigned)P, warps * 32, smem, st>>>(a, dt4, P);
+    }
     return cudaGetLastError();
 }
 

@@ -639,6 +639,7 @@ int* wide_eval_error_word(void* work, const LevelGeom& g, long P) {
 
 cudaError_t launch_wide_eval(const u32* in, long in_stride, const LevelGeom& g, u32* out, uint8_t* sgn,
                              long P, void* work, cudaStream_t st) {
+    note_kernel("wide_eval passes");
     size_t stat_off, swap_off, cnt_off;
     wide_eval_parts(g, P, &stat_off, &swap_off, &cnt_off);
     char* base = (char*)work;
@@ -689,6 +690,7 @@ cudaError_t launch_wide_eval(const u32* in, long in_stride, const LevelGeom& g, 
 cudaError_t launch_wide_interp(const LevelGeom& g, const u32* y, const uint8_t* su, const uint8_t* sv,
                                u32* out, long out_stride, int out_len, void* work, long P,
                                cudaStream_t st) {
+    note_kernel("wide_interp passes");
     int* err_dev = wide_error_word(work, g, P);
     static const WideDivTable dt = make_wide_div_table();
     const int n = g.n;

@@ -84,6 +84,8 @@ _SIGS = {
     "tc_interp_matrix_table": (ctypes.c_int, [ctypes.c_int, _i64p, _vp, _vp]),
     "tc_toom_interpolate_noalloc": (ctypes.c_int, [_sz, _sz, ctypes.c_int, _u32p, _sz, _u8p, _u8p,
                                                    _u32p, _sz, _vp]),
+    "tc_peak_madc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _u32p, _vp,
+                                    ctypes.POINTER(ctypes.c_double)]),
     "tc_serve_submit": (ctypes.c_int, [_vp, _u32p, _sz, _u32p, _sz, _u32p,
                                        ctypes.POINTER(ctypes.c_uint64)]),
     "tc_serve_poll": (ctypes.c_int, [_vp, ctypes.c_uint64]),
@@ -476,7 +478,7 @@ def tc_serve_stop(ctx: Context):
 class tc_phase_stat(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("level", ctypes.c_int), ("launches", ctypes.c_int),
                 ("ms", ctypes.c_double), ("bytes", ctypes.c_double),
-                ("limb_products", ctypes.c_double)]
+                ("limb_products", ctypes.c_double), ("kernel", ctypes.c_char * 48)]
 
 
 PHASE_NAMES = {0: "evaluate", 1: "base_case", 2: "interpolate"}
@@ -487,12 +489,13 @@ def tc_profile_enable(ctx: Context, on: bool = True):
 
 
 def tc_profile_read(ctx: Context):
-    """List of dicts: kind, level, launches, ms, bytes, limb_products."""
+    """List of dicts: kind, level, kernel, launches, ms, bytes, limb_products."""
     arr = (tc_phase_stat * 64)()
     n = ctypes.c_int()
     _check(lib().tc_profile_read(ctx.handle, arr, 64, ctypes.byref(n)), "tc_profile_read")
-    return [{"kind": PHASE_NAMES[a.kind], "level": a.level, "launches": a.launches, "ms": a.ms,
-             "bytes": a.bytes, "limb_products": a.limb_products} for a in arr[:n.value]]
+    return [{"kind": PHASE_NAMES[a.kind], "level": a.level, "kernel": a.kernel.decode(),
+             "launches": a.launches, "ms": a.ms, "bytes": a.bytes,
+             "limb_products": a.limb_products} for a in arr[:n.value]]
 
 
 # ---- limb helpers (numpy uint32 <-> torch int32) ----
@@ -504,3 +507,12 @@ def to_device(x: np.ndarray, device="cuda"):
 
 def to_numpy(t) -> np.ndarray:
     return t.detach().cpu().numpy().view(np.uint32)
+
+
+def tc_peak_madc(blocks: int, iters: int, sink, stream=None) -> float:
+    """Enqueue the base case's register-only multiply-accumulate loop; returns
+    the number of limb products the launch performs (time it with events)."""
+    n = ctypes.c_double()
+    _check(lib().tc_peak_madc(int(blocks), int(iters), _ptr(sink), _stream(stream),
+                              ctypes.byref(n)), "tc_peak_madc")
+    return n.value
