@@ -97,9 +97,10 @@ def table_plan(limbs: int):
         for line in f:
             if line.startswith("#") or not line.strip():
                 continue
-            parts = [int(x) for x in line.split()]
+            words = line.split()
+            parts = [int(x) for x in words[:2 + int(words[1])]]
             if limbs <= parts[0]:
-                return parts[2:2 + parts[1]]
+                return parts[2:] + (["ntt"] if words[-1] == "ntt" else [])
     return None
 
 

@@ -20,7 +20,14 @@
  * - Output buffers must not overlap input buffers.
  * - `stream` is a cudaStream_t passed as void*; NULL means the legacy default
  *   stream.  Calls are asynchronous with respect to the host unless stated;
- *   results are valid once the stream has completed.
+ *   results are valid once the stream has completed.  The multiply calls
+ *   (tc_mul, tc_sqr, tc_mul_uniform, tc_mul_batch) never wait for the device,
+ *   except when the context's scratch or pinned staging has to grow (the
+ *   first call of a larger shape allocates); so they can be captured into a
+ *   CUDA graph once the context has run the same shape outside the capture.
+ * - Levels with few huge products run segment-parallel with bounded device
+ *   waits.  A wait that gives up (never expected: it needs a stalled GPU) sets
+ *   a sticky error word of the context instead of hanging; tc_check reports it.
  * - The caller owns every buffer it passes.  The context owns its scratch
  *   memory (allocated with cudaMalloc, never above the context's budget).
  * - Errors are returned as tc_status; nothing aborts, traps or throws.
@@ -54,29 +61,44 @@ typedef enum {
 #define TC_MAX_LEVELS 8
 
 /*
- * Recursion plan.  levels = number of Toom levels above the schoolbook base
- * case (0 = plain schoolbook); B[l] is the number of blocks at level l
+ * Recursion plan.  levels = number of Toom levels above the base product
+ * (0 = the base product alone); B[l] is the number of blocks at level l
  * (2 <= B[l] <= 32).  Block size at a level of operand length s is
  * b = ceil(s / B); each evaluation value has e = b + ceil((n(n-1)+1)/32)
  * limbs (n = B-1), which is the operand length of the next level.
- * Passing NULL for a `const tc_opts*` lets the library choose the plan
- * (autotuned table if loaded, else a built-in rule).
+ * base selects the product below the last level: TC_BASE_SCHOOLBOOK (the
+ * plain schoolbook of Section 6; leaves of at most 1024 limbs when levels > 0)
+ * or TC_BASE_NTT (an exact number-theoretic-transform product: Toom-Cook as
+ * the parallel wrapper around a fast multiply, Section 5; leaves of at most
+ * 2^24 limbs).  Passing NULL for a `const tc_opts*` lets the library choose
+ * the plan (autotuned table if loaded, else a built-in rule).
  */
+#define TC_BASE_SCHOOLBOOK 0
+#define TC_BASE_NTT 1
 typedef struct {
     int levels;
     int B[TC_MAX_LEVELS];
+    int base;
 } tc_opts;
 
 /* Create a context on CUDA device `device` whose scratch never exceeds
  * `hbm_budget_bytes` (0 = 3/4 of the device's free memory).
  * `tune_table_path` (nullable) names a plan table written by the autotuner:
- * text lines "<max_limbs> <levels> <B0> <B1> ...", ascending max_limbs.
+ * text lines "<max_limbs> <levels> <B0> <B1> ... [ntt]", ascending max_limbs
+ * ("ntt" selects the transform base product).
  * On success *ctx is set and TC_OK returned. */
 tc_status tc_create(tc_ctx **ctx, int device, size_t hbm_budget_bytes,
                     const char *tune_table_path);
 
 /* Free the context and its scratch (synchronises the device first). */
 void tc_destroy(tc_ctx *ctx);
+
+/* Wait for `stream`, then report the context's sticky bounded-wait error word:
+ * TC_ETIMEOUT (the word is cleared) if a segment-parallel level of any multiply
+ * call on this context since the last check gave up a wait -- those results are
+ * invalid -- else TC_OK.  Prepared batches and pipes keep their own words
+ * (tc_batch_check, tc_pipe_wait). */
+tc_status tc_check(tc_ctx *ctx, void *stream);
 
 /* The plan the library would use for balanced operands of `limbs` limbs. */
 tc_status tc_plan_for(tc_ctx *ctx, size_t limbs, tc_opts *plan_out);
@@ -135,7 +157,8 @@ tc_status tc_mul_batch(tc_ctx *ctx, size_t count,
  * the prepared offsets (products of length 0 get zero-filled outputs).  Runs of
  * one batch must not overlap in time: they share its scratch.
  * tc_batch_check waits for `stream` and returns TC_ETIMEOUT if a bounded wait
- * of a segment-parallel level gave up in the last run, else TC_OK.
+ * of a segment-parallel level gave up in any run since the last check (and
+ * clears that state), else TC_OK.
  * tc_batch_destroy frees the batch (NULL is ignored).
  */
 typedef struct tc_batch tc_batch;
@@ -179,10 +202,12 @@ tc_status tc_mul_uniform_host(tc_ctx *ctx, size_t count, size_t limbs,
  * valid and unmodified (OUT unread) until tc_pipe_wait returns.  `square`
  * fixes at creation whether batches are squares (Bv ignored, A == Bv
  * semantics) or products.  tc_pipe_wait blocks until every submitted batch is
- * complete.  Errors: TC_EINVAL (null or zero arguments, a context of another
- * device), TC_ENOMEM (the pipe's memory exceeds the context's budget),
- * TC_EDEVICE; after an error from tc_pipe_submit or tc_pipe_wait the pipe's
- * state is undefined: destroy it.  tc_pipe_destroy waits for the pipe and
+ * complete; it returns TC_ETIMEOUT if a bounded wait of a segment-parallel
+ * level gave up in any batch since the last wait.  Errors: TC_EINVAL (null or
+ * zero arguments, a context of another device), TC_ENOMEM (the pipe's memory
+ * exceeds the context's budget), TC_EDEVICE; after an error from
+ * tc_pipe_submit or tc_pipe_wait the pipe's state is undefined: destroy it.
+ * tc_pipe_destroy waits for the pipe and
  * frees it (NULL ignored).
  */
 typedef struct tc_pipe tc_pipe;
@@ -206,6 +231,30 @@ void tc_pipe_destroy(tc_pipe *pipe);
 tc_status tc_schoolbook(size_t count, size_t limbs, const uint32_t *A, size_t lda,
                         const uint32_t *Bv, size_t ldb, uint32_t *OUT, size_t ldo,
                         void *stream);
+
+/*
+ * Base product by number-theoretic transform (the fast multiply that Section 5
+ * wraps in Toom-Cook; the paper's is GMP's FFT, this one is exact by
+ * construction): `count` rows of `limbs` x `limbs` limbs as in tc_schoolbook
+ * (limbs <= 2^24), 2*limbs limbs written at OUT + k*ldo.  Each operand is
+ * read as 16-bit digits; the digit vectors are convolved by a transform of
+ * N = 2^n >= 4*limbs points modulo the prime p = 2^64 - 2^32 + 1 (every
+ * convolution coefficient is below N 2^32 < p, so the result is exact), and
+ * the coefficients are carried into limbs.  A == Bv with lda == ldb squares
+ * (one forward transform).  `work` is device scratch of
+ * tc_ntt_work_bytes(count, limbs) bytes, 16-byte aligned; otherwise
+ * TC_EINVAL.  The first call for a transform length uploads that length's
+ * root tables (a small device allocation kept until exit).
+ */
+tc_status tc_ntt_mul(size_t count, size_t limbs, const uint32_t *A, size_t lda,
+                     const uint32_t *Bv, size_t ldb, uint32_t *OUT, size_t ldo, void *work,
+                     void *stream);
+size_t tc_ntt_work_bytes(size_t count, size_t limbs);
+
+/* Host only: the primitive 2^log2n-th root of unity modulo p = 2^64 - 2^32 + 1
+ * the transform uses (7^((p-1)/2^log2n), 7 generating the multiplicative
+ * group); TC_EINVAL unless 0 <= log2n <= 32. */
+tc_status tc_ntt_root(int log2n, uint64_t *root);
 
 /*
  * Evaluation (Section 4, eq. 4.1-4.2; points of Section 6).  Each of `count`
@@ -355,6 +404,19 @@ tc_status tc_profile_read(tc_ctx *ctx, tc_phase_stat *out, int cap, int *n);
  * for non-positive sizes or null pointers.
  */
 tc_status tc_peak_madc(int blocks, int iters, uint32_t *sink, void *stream, double *limb_products);
+
+/*
+ * Failure-detection test hook (the paper has no counterpart).  On the current
+ * device, from the next launch on: every bounded wait of the segment-parallel
+ * passes gives up after `polls` polls of at least 64 ns (0 restores the default
+ * of 2^22 polls, about a quarter second), and if `withhold` is nonzero the first
+ * segment of every segment-parallel add/subtract chain does not publish its
+ * carry, so the waits behind it run out and the calls report TC_ETIMEOUT
+ * (tc_check, tc_batch_check, tc_pipe_wait, a serving poll) instead of
+ * hanging.  Results computed while `withhold` is set are wrong by design.  Not
+ * for concurrent use with other work on the device.  TC_EINVAL if polls < 0.
+ */
+tc_status tc_test_bounded_waits(int polls, int withhold);
 
 /* Message for a status code (static string). */
 const char *tc_strerror(tc_status s);

@@ -63,6 +63,7 @@ tc_opts default_plan(size_t s) {
 
 bool plan_valid(const tc_opts& o, size_t s) {
     if (o.levels < 0 || o.levels > TC_MAX_LEVELS) return false;
+    if (o.base != TC_BASE_SCHOOLBOOK && o.base != TC_BASE_NTT) return false;
     size_t L = s;
     for (int l = 0; l < o.levels; ++l) {
         if (o.B[l] < 2 || o.B[l] > 32) return false;
@@ -70,6 +71,7 @@ bool plan_valid(const tc_opts& o, size_t s) {
         LevelGeom g = make_level((int)L, o.B[l]);
         L = (size_t)g.e;
     }
+    if (o.base == TC_BASE_NTT) return L <= (size_t)NTT_MAX_LIMBS;
     return o.levels == 0 || L <= (size_t)LEAF_MAX;  // no levels: plain schoolbook, any length
 }
 
@@ -104,6 +106,13 @@ BatchLayout layout_for(size_t count, size_t s, const tc_opts& o, bool square) {
         sl = g.e;
     }
     L.P.push_back(P);
+    L.base = o.base;
+    if (o.base == TC_BASE_NTT) {  // transform scratch of the base products
+        L.ntt = off;
+        off = align256(off + ntt_work_bytes(sl, P, square));
+        L.total = off;
+        return L;
+    }
     if (o.levels == 0 && s > (size_t)LEAF_MAX) {  // column buffer of the large schoolbook
         L.work.push_back(off);
         off = align256(off + schoolbook_big_bytes((int)s, (long)count));
@@ -164,14 +173,26 @@ struct PhaseTimer {
 };
 
 // Run a uniform batch whose scratch is `base` laid out by `L`.
+static __global__ void or_error_kernel(int* sticky, const int* word) {
+    if (threadIdx.x == 0 && *word) *sticky = 1;
+}
+
+cudaError_t launch_or_error(int* sticky, const int* word, cudaStream_t st) {
+    or_error_kernel<<<1, 32, 0, st>>>(sticky, word);
+    return cudaGetLastError();
+}
+
 tc_status run_uniform(const BatchLayout& L, char* base, size_t count, size_t s, const u32* A,
                       long lda, const u32* Bm, long ldb, u32* OUT, long ldo, bool square,
-                      cudaStream_t st, tc_ctx* ctx) {
+                      cudaStream_t st, tc_ctx* ctx, int* sticky) {
     PhaseTimer pt{ctx, st};
     const int D = (int)L.g.size();
     if (D == 0) {
         pt.begin(1, 0, 4.0 * count * 4 * s, (double)count * s * s);
-        if (s > (size_t)LEAF_MAX)
+        if (L.base == TC_BASE_NTT)
+            CK(launch_ntt_mul(A, lda, square ? A : Bm, square ? lda : ldb, OUT, ldo, (int)s,
+                              (long)count, square, base + L.ntt, st));
+        else if (s > (size_t)LEAF_MAX)
             CK(launch_schoolbook_big(A, lda, square ? A : Bm, square ? lda : ldb, OUT, ldo, (int)s,
                                      (long)count, reinterpret_cast<u32*>(base + L.work[0]), st));
         else
@@ -209,8 +230,12 @@ tc_status run_uniform(const BatchLayout& L, char* base, size_t count, size_t s, 
     }
     const LevelGeom& gl = L.g[D - 1];
     pt.begin(1, D, 4.0 * L.P[D] * 4 * gl.e, (double)L.P[D] * gl.e * gl.e);
-    CK(launch_leaf(inU, strU, inV, strV, reinterpret_cast<u32*>(base + L.prod[D - 1]), gl.ystride,
-                   gl.e, L.P[D], st));
+    if (L.base == TC_BASE_NTT)
+        CK(launch_ntt_mul(inU, strU, inV, strV, reinterpret_cast<u32*>(base + L.prod[D - 1]),
+                          gl.ystride, gl.e, L.P[D], square, base + L.ntt, st));
+    else
+        CK(launch_leaf(inU, strU, inV, strV, reinterpret_cast<u32*>(base + L.prod[D - 1]), gl.ystride,
+                       gl.e, L.P[D], st));
     pt.end();
     for (int l = D - 1; l >= 0; --l) {
         const LevelGeom& g = L.g[l];
@@ -233,20 +258,15 @@ tc_status run_uniform(const BatchLayout& L, char* base, size_t count, size_t s, 
                          2 * g.s, work, L.P[l], st));
         pt.end();
     }
-    // segment-parallel levels: report a bounded wait that gave up (never expected)
-    if (ctx) {
+    // segment-parallel levels: a bounded wait that gave up (never expected) is
+    // carried into the caller's sticky word by a kernel; nothing waits here
+    if (sticky) {
         for (int l = 0; l < D; ++l) {
-            int* words[2] = {nullptr, nullptr};
-            if (use_wide(L.g[l], L.P[l])) words[0] = wide_error_word(base + L.work[l], L.g[l], L.P[l]);
+            if (use_wide(L.g[l], L.P[l]))
+                CK(launch_or_error(sticky, wide_error_word(base + L.work[l], L.g[l], L.P[l]), st));
             if (use_wide_eval(L.g[l], L.P[l]))
-                words[1] = wide_eval_error_word(base + L.evwork[l], L.g[l], L.P[l]);
-            for (int* w : words) {
-                if (!w) continue;
-                int flag = 0;
-                CK(cudaMemcpyAsync(&flag, w, sizeof(int), cudaMemcpyDeviceToHost, st));
-                CK(cudaStreamSynchronize(st));
-                if (flag) return TC_ETIMEOUT;
-            }
+                CK(launch_or_error(sticky, wide_eval_error_word(base + L.evwork[l], L.g[l], L.P[l]),
+                                   st));
         }
     }
     return TC_OK;
@@ -276,6 +296,8 @@ static bool load_table(const char* path, std::vector<std::pair<size_t, tc_opts>>
             if (sscanf(line + pos, "%d%n", &o.B[l], &n) != 1) { ok = false; break; }
             pos += n;
         }
+        char word[16];
+        if (ok && sscanf(line + pos, "%15s", word) == 1 && strcmp(word, "ntt") == 0) o.base = TC_BASE_NTT;
         if (ok) out.push_back({(size_t)mx, o});
     }
     fclose(f);
@@ -299,6 +321,13 @@ extern "C" tc_status tc_create(tc_ctx** ctx, int device, size_t hbm_budget_bytes
         delete c;
         return TC_EINVAL;
     }
+    cudaError_t e = cudaMalloc(&c->err_dev, 256);
+    if (e == cudaSuccess) e = cudaMemset(c->err_dev, 0, 256);
+    if (e != cudaSuccess) {
+        if (c->err_dev) cudaFree(c->err_dev);
+        delete c;
+        return tc_fail_cuda(e);
+    }
     *ctx = c;
     return TC_OK;
 }
@@ -312,6 +341,11 @@ extern "C" void tc_destroy(tc_ctx* ctx) {
     for (auto e : ctx->event_pool) cudaEventDestroy(e);
     if (ctx->arena) cudaFree(ctx->arena);
     if (ctx->aux) cudaFree(ctx->aux);
+    if (ctx->err_dev) cudaFree(ctx->err_dev);
+    for (int i = 0; i < 2; ++i) {
+        if (ctx->pin[i]) cudaFreeHost(ctx->pin[i]);
+        if (ctx->pin_ev[i]) cudaEventDestroy(ctx->pin_ev[i]);
+    }
     delete ctx;
 }
 
@@ -349,7 +383,7 @@ static tc_status mul_uniform(tc_ctx* ctx, size_t count, size_t limbs, const u32*
     s = ensure_arena(ctx, L.total, st);
     if (s) return s;
     return run_uniform(L, (char*)ctx->arena, count, limbs, A, (long)lda, Bm, (long)ldb, OUT,
-                       (long)ldo, square, st, ctx);
+                       (long)ldo, square, st, ctx, ctx->err_dev);
 }
 
 extern "C" tc_status tc_mul_uniform(tc_ctx* ctx, size_t count, size_t limbs, const uint32_t* A,
@@ -409,6 +443,7 @@ struct tc_pipe {
     size_t in_bytes = 0, out_bytes = 0, scratch = 0;
     cudaStream_t s_in = nullptr, s_run = nullptr, s_out = nullptr;
     cudaEvent_t in_done[2] = {}, run_done[2] = {}, out_done[2] = {};
+    int* err_dev = nullptr;  // sticky bounded-wait error word of the pipe's batches
     long submitted = 0;
     u32* slot_ptr(int slot, int which) const {  // which: 0 A, 1 B, 2 OUT
         const size_t per = 2 * align256(in_bytes) + align256(out_bytes);
@@ -431,6 +466,7 @@ static void pipe_free(tc_pipe* p) {
     if (p->s_run) cudaStreamDestroy(p->s_run);
     if (p->s_out) cudaStreamDestroy(p->s_out);
     if (p->mem) cudaFree(p->mem);
+    if (p->err_dev) cudaFree(p->err_dev);
     delete p;
 }
 
@@ -458,6 +494,8 @@ extern "C" tc_status tc_pipe_create(tc_ctx* ctx, size_t count, size_t limbs, int
         p->mem = nullptr;
         return TC_ENOMEM;
     }
+    CK(cudaMalloc(&p->err_dev, 256));
+    CK(cudaMemset(p->err_dev, 0, 256));
     CK(cudaStreamCreateWithFlags(&p->s_in, cudaStreamNonBlocking));
     CK(cudaStreamCreateWithFlags(&p->s_run, cudaStreamNonBlocking));
     CK(cudaStreamCreateWithFlags(&p->s_out, cudaStreamNonBlocking));
@@ -488,7 +526,8 @@ extern "C" tc_status tc_pipe_submit(tc_ctx* ctx, tc_pipe* p, const uint32_t* A, 
     CK(cudaStreamWaitEvent(p->s_run, p->in_done[slot], 0));
     CK(cudaStreamWaitEvent(p->s_run, p->out_done[slot], 0));
     tc_status s = run_uniform(p->L, p->mem, p->count, p->limbs, dA, (long)p->limbs, dB,
-                              (long)p->limbs, dO, (long)(2 * p->limbs), p->square, p->s_run, ctx);
+                              (long)p->limbs, dO, (long)(2 * p->limbs), p->square, p->s_run, ctx,
+                              p->err_dev);
     if (s) return s;
     CK(cudaEventRecord(p->run_done[slot], p->s_run));
     // copy-out
@@ -505,6 +544,12 @@ extern "C" tc_status tc_pipe_wait(tc_pipe* p) {
     CK(cudaStreamSynchronize(p->s_out));  // its last copy waits on every earlier step
     CK(cudaStreamSynchronize(p->s_run));
     CK(cudaStreamSynchronize(p->s_in));
+    int flag = 0;
+    CK(cudaMemcpy(&flag, p->err_dev, sizeof flag, cudaMemcpyDeviceToHost));
+    if (flag) {
+        CK(cudaMemset(p->err_dev, 0, sizeof flag));
+        return TC_ETIMEOUT;
+    }
     return TC_OK;
 }
 
@@ -565,8 +610,30 @@ static bool batch_tables_valid(size_t count, const int64_t* a_off, const int64_t
     return true;
 }
 
+// Pinned host staging for `bytes` of index tables (one of two buffers, in turn).
+// A buffer is rewritten only after the copy that last read it has completed:
+// the copy was enqueued ahead of that call's kernels, so this waits for at most
+// the work enqueued before the previous call, never for the previous call itself.
+static tc_status stage_tables(tc_ctx* ctx, size_t bytes, void** host) {
+    const int t = ctx->pin_turn;
+    if (ctx->pin_ev[t]) CK(cudaEventSynchronize(ctx->pin_ev[t]));
+    else CK(cudaEventCreateWithFlags(&ctx->pin_ev[t], cudaEventDisableTiming));
+    if (bytes > ctx->pin_bytes[t]) {  // grow (allocation path)
+        if (ctx->pin[t]) CK(cudaFreeHost(ctx->pin[t]));
+        ctx->pin[t] = nullptr;
+        ctx->pin_bytes[t] = 0;
+        const size_t want = std::max(bytes, (size_t)64 << 10);
+        CK(cudaHostAlloc(&ctx->pin[t], want, cudaHostAllocDefault));
+        ctx->pin_bytes[t] = want;
+    }
+    *host = ctx->pin[t];
+    return TC_OK;
+}
+
 // Products listed by (offset, length) triples; all device limb buffers, host index arrays
-// (validated by batch_tables_valid).
+// (validated by batch_tables_valid).  Asynchronous: the tables of every size class
+// go to the device in one copy from pinned staging, and the classes run one after
+// another on the stream sharing one scratch region.
 static tc_status mul_general(tc_ctx* ctx, size_t count, const u32* A, const int64_t* a_off,
                              const int64_t* a_len, const u32* Bm, const int64_t* b_off,
                              const int64_t* b_len, u32* OUT, const int64_t* out_off,
@@ -584,70 +651,75 @@ static tc_status mul_general(tc_ctx* ctx, size_t count, const u32* A, const int6
         }
         items.push_back({k, size_class(L)});
     }
+    if (items.empty()) return TC_OK;
     std::sort(items.begin(), items.end(), [](const Item& x, const Item& y) { return x.cls < y.cls; });
-    size_t i = 0;
-    while (i < items.size()) {
+    struct Class { size_t s, cnt, first; BatchLayout L; };
+    std::vector<Class> classes;
+    size_t need = 0;
+    for (size_t i = 0; i < items.size();) {
         size_t j = i;
         while (j < items.size() && items[j].cls == items[i].cls) ++j;
-        const size_t s = items[i].cls, cnt = j - i;
+        Class c;
+        c.s = items[i].cls;
+        c.cnt = j - i;
+        c.first = i;
         // a caller's plan applies to every size class it is valid for
-        tc_opts o = (opts && plan_valid(*opts, s)) ? *opts : plan_for(ctx, s);
-        BatchLayout L = layout_for(cnt, s, o, false);
-        // index arrays + padded rows + outputs after the level scratch
-        const size_t idx_bytes = align256(cnt * 8);
-        const size_t rows_bytes = align256(cnt * s * 4);
-        const size_t outs_bytes = align256(cnt * 2 * s * 4);
-        const size_t extra = 5 * idx_bytes + 2 * rows_bytes + outs_bytes;
-        tc_status e = ensure_arena(ctx, L.total + extra, st);
-        if (e) return e;
-        char* base = (char*)ctx->arena;
-        char* x = base + L.total;
-        int64_t* d_aoff = (int64_t*)x; x += idx_bytes;
-        int64_t* d_alen = (int64_t*)x; x += idx_bytes;
-        int64_t* d_boff = (int64_t*)x; x += idx_bytes;
-        int64_t* d_blen = (int64_t*)x; x += idx_bytes;
-        int64_t* d_ooff = (int64_t*)x; x += idx_bytes;
-        u32* rA = (u32*)x; x += rows_bytes;
-        u32* rB = (u32*)x; x += rows_bytes;
-        u32* rO = (u32*)x;
-        std::vector<int64_t> h(5 * cnt);
-        for (size_t t = 0; t < cnt; ++t) {
-            const size_t k = items[i + t].k;
-            h[t] = a_off[k];
-            h[cnt + t] = a_len[k];
-            h[2 * cnt + t] = b_off[k];
-            h[3 * cnt + t] = b_len[k];
-            h[4 * cnt + t] = out_off[k];
-        }
-        // pageable copies are synchronous with respect to the host buffer: safe for `h`
-        CK(cudaMemcpyAsync(d_aoff, h.data(), cnt * 8, cudaMemcpyHostToDevice, st));
-        CK(cudaMemcpyAsync(d_alen, h.data() + cnt, cnt * 8, cudaMemcpyHostToDevice, st));
-        CK(cudaMemcpyAsync(d_boff, h.data() + 2 * cnt, cnt * 8, cudaMemcpyHostToDevice, st));
-        CK(cudaMemcpyAsync(d_blen, h.data() + 3 * cnt, cnt * 8, cudaMemcpyHostToDevice, st));
-        CK(cudaMemcpyAsync(d_ooff, h.data() + 4 * cnt, cnt * 8, cudaMemcpyHostToDevice, st));
+        const tc_opts o = (opts && plan_valid(*opts, c.s)) ? *opts : plan_for(ctx, c.s);
+        c.L = layout_for(c.cnt, c.s, o, false);
+        need = std::max(need, c.L.total + 2 * align256(c.cnt * c.s * 4) + align256(c.cnt * 2 * c.s * 4));
+        classes.push_back(std::move(c));
+        i = j;
+    }
+    // index tables: aoff, alen, boff, blen, ooff, olen, each N long, in class order
+    const size_t N = items.size();
+    const size_t tab_bytes = 6 * N * 8;
+    tc_status e = ensure_arena(ctx, align256(need) + align256(tab_bytes), st);
+    if (e) return e;
+    void* hv = nullptr;
+    if ((e = stage_tables(ctx, tab_bytes, &hv))) return e;
+    int64_t* h = static_cast<int64_t*>(hv);
+    for (size_t t = 0; t < N; ++t) {
+        const size_t k = items[t].k;
+        h[t] = a_off[k];
+        h[N + t] = a_len[k];
+        h[2 * N + t] = b_off[k];
+        h[3 * N + t] = b_len[k];
+        h[4 * N + t] = out_off[k];
+        h[5 * N + t] = a_len[k] + b_len[k];
+    }
+    char* base = (char*)ctx->arena;
+    int64_t* dtab = (int64_t*)(base + align256(need));
+    CK(cudaMemcpyAsync(dtab, h, tab_bytes, cudaMemcpyHostToDevice, st));
+    CK(cudaEventRecord(ctx->pin_ev[ctx->pin_turn], st));
+    ctx->pin_turn ^= 1;
+    for (const Class& c : classes) {
+        const size_t s = c.s, cnt = c.cnt;
+        u32* rA = (u32*)(base + c.L.total);
+        u32* rB = (u32*)((char*)rA + align256(cnt * s * 4));
+        u32* rO = (u32*)((char*)rB + align256(cnt * s * 4));
+        const int64_t* aoff = dtab + c.first;
+        const int64_t* alen = dtab + N + c.first;
+        const int64_t* boff = dtab + 2 * N + c.first;
+        const int64_t* blen = dtab + 3 * N + c.first;
+        const int64_t* ooff = dtab + 4 * N + c.first;
+        const int64_t* olen = dtab + 5 * N + c.first;
         for (size_t c0 = 0; c0 < cnt; c0 += 65535) {
             const int cc = (int)std::min<size_t>(65535, cnt - c0);
             dim3 grid((unsigned)std::min<size_t>((s + 255) / 256, 64), cc);
-            gather_rows<<<grid, 256, 0, st>>>(A, d_aoff + c0, d_alen + c0, (int)s, rA + c0 * s, cc);
-            gather_rows<<<grid, 256, 0, st>>>(Bm, d_boff + c0, d_blen + c0, (int)s, rB + c0 * s, cc);
+            gather_rows<<<grid, 256, 0, st>>>(A, aoff + c0, alen + c0, (int)s, rA + c0 * s, cc);
+            gather_rows<<<grid, 256, 0, st>>>(Bm, boff + c0, blen + c0, (int)s, rB + c0 * s, cc);
         }
         CK(cudaGetLastError());
-        e = run_uniform(L, base, cnt, s, rA, (long)s, rB, (long)s, rO, (long)(2 * s), false, st, ctx);
+        e = run_uniform(c.L, base, cnt, s, rA, (long)s, rB, (long)s, rO, (long)(2 * s), false, st, ctx,
+                        ctx->err_dev);
         if (e) return e;
-        // out length per product = a_len + b_len: reuse d_alen as a scratch? compute on host
-        std::vector<int64_t> olen(cnt);
-        for (size_t t = 0; t < cnt; ++t) olen[t] = h[cnt + t] + h[3 * cnt + t];
-        CK(cudaMemcpyAsync(d_alen, olen.data(), cnt * 8, cudaMemcpyHostToDevice, st));
         for (size_t c0 = 0; c0 < cnt; c0 += 65535) {
             const int cc = (int)std::min<size_t>(65535, cnt - c0);
             dim3 grid((unsigned)std::min<size_t>((2 * s + 255) / 256, 64), cc);
-            scatter_rows<<<grid, 256, 0, st>>>(rO + c0 * 2 * s, (int)(2 * s), d_ooff + c0,
-                                               d_alen + c0, OUT, cc);
+            scatter_rows<<<grid, 256, 0, st>>>(rO + c0 * 2 * s, (int)(2 * s), ooff + c0, olen + c0,
+                                               OUT, cc);
         }
         CK(cudaGetLastError());
-        // the host vectors die at scope end: make sure the copies have consumed them
-        CK(cudaStreamSynchronize(st));
-        i = j;
     }
     return TC_OK;
 }
@@ -684,7 +756,10 @@ struct tc_batch {
     size_t total = 0;
     char* scratch = nullptr;    // device: max over classes of level scratch + rows + outputs
     size_t scratch_bytes = 0;
+    int* err_dev = nullptr;     // device: sticky bounded-wait error word of the runs
 };
+
+extern "C" void tc_batch_destroy(tc_batch* bt);
 
 static size_t class_extra(size_t cnt, size_t s) {
     return 2 * align256(cnt * s * 4) + align256(cnt * 2 * s * 4);
@@ -737,20 +812,26 @@ extern "C" tc_status tc_batch_prepare(tc_ctx* ctx, size_t count, const int64_t* 
     }
     if (need > ctx->budget) return TC_ENOMEM;
     bt->total = N;
+    // on any failure below the partly built batch is released with its device memory
+    auto fail = [&](tc_status st) {
+        tc_batch_destroy(bt.release());
+        return st;
+    };
+    if (cudaMalloc(&bt->err_dev, 256) != cudaSuccess) { cudaGetLastError(); return fail(TC_ENOMEM); }
+    cudaError_t e = cudaMemset(bt->err_dev, 0, 256);
+    if (e != cudaSuccess) return fail(tc_fail_cuda(e));
     if (N) {
-        if (cudaMalloc(&bt->tables, h.size() * 8) != cudaSuccess) { cudaGetLastError(); return TC_ENOMEM; }
+        if (cudaMalloc(&bt->tables, h.size() * 8) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(TC_ENOMEM);
+        }
         if (cudaMalloc(&bt->scratch, need) != cudaSuccess) {
             cudaGetLastError();
-            cudaFree(bt->tables);
-            return TC_ENOMEM;
+            return fail(TC_ENOMEM);
         }
         bt->scratch_bytes = need;
-        const cudaError_t e = cudaMemcpy(bt->tables, h.data(), h.size() * 8, cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) {
-            cudaFree(bt->tables);
-            cudaFree(bt->scratch);
-            return tc_fail_cuda(e);
-        }
+        e = cudaMemcpy(bt->tables, h.data(), h.size() * 8, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return fail(tc_fail_cuda(e));
     }
     *out = bt.release();
     return TC_OK;
@@ -785,7 +866,7 @@ extern "C" tc_status tc_batch_run(tc_ctx* ctx, const tc_batch* bt, const uint32_
         CK(cudaGetLastError());
         // no context: no phase events and no host read-back inside a possibly captured run
         tc_status e = run_uniform(c.L, base, c.cnt, c.s, rA, (long)c.s, rB, (long)c.s, rO,
-                                  (long)(2 * c.s), false, st, nullptr);
+                                  (long)(2 * c.s), false, st, nullptr, bt->err_dev);
         if (e) return e;
         for (size_t c0 = 0; c0 < c.cnt; c0 += 65535) {
             const int cc = (int)std::min<size_t>(65535, c.cnt - c0);
@@ -801,25 +882,34 @@ extern "C" tc_status tc_batch_run(tc_ctx* ctx, const tc_batch* bt, const uint32_
 extern "C" size_t tc_batch_scratch_bytes(const tc_batch* bt) { return bt ? bt->scratch_bytes : 0; }
 
 // After a run (direct or replayed) has completed on `stream`: TC_ETIMEOUT if a
-// bounded wait of a segment-parallel level gave up, else TC_OK.  Synchronises.
+// bounded wait of a segment-parallel level gave up in any run since the last
+// check (the word is cleared), else TC_OK.  Synchronises.
 extern "C" tc_status tc_batch_check(tc_ctx* ctx, const tc_batch* bt, void* stream) {
     if (!ctx || !bt || bt->device != ctx->device) return TC_EINVAL;
     CK(cudaSetDevice(ctx->device));
     cudaStream_t st = (cudaStream_t)stream;
-    for (const auto& c : bt->classes) {
-        for (size_t l = 0; l < c.L.g.size(); ++l) {
-            int* words[2] = {nullptr, nullptr};
-            if (use_wide(c.L.g[l], c.L.P[l])) words[0] = wide_error_word(bt->scratch + c.L.work[l], c.L.g[l], c.L.P[l]);
-            if (use_wide_eval(c.L.g[l], c.L.P[l]))
-                words[1] = wide_eval_error_word(bt->scratch + c.L.evwork[l], c.L.g[l], c.L.P[l]);
-            for (int* w : words) {
-                if (!w) continue;
-                int flag = 0;
-                CK(cudaMemcpyAsync(&flag, w, sizeof(int), cudaMemcpyDeviceToHost, st));
-                CK(cudaStreamSynchronize(st));
-                if (flag) return TC_ETIMEOUT;
-            }
-        }
+    CK(cudaStreamSynchronize(st));
+    int flag = 0;
+    CK(cudaMemcpy(&flag, bt->err_dev, sizeof flag, cudaMemcpyDeviceToHost));
+    if (flag) {
+        CK(cudaMemset(bt->err_dev, 0, sizeof flag));
+        return TC_ETIMEOUT;
+    }
+    return TC_OK;
+}
+
+/* The context's sticky bounded-wait error word: waits for `stream`, then
+ * TC_ETIMEOUT (and clears the word) if a segment-parallel level of any call on
+ * this context since the last check gave up a wait. */
+extern "C" tc_status tc_check(tc_ctx* ctx, void* stream) {
+    if (!ctx) return TC_EINVAL;
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    int flag = 0;
+    CK(cudaMemcpy(&flag, ctx->err_dev, sizeof flag, cudaMemcpyDeviceToHost));
+    if (flag) {
+        CK(cudaMemset(ctx->err_dev, 0, sizeof flag));
+        return TC_ETIMEOUT;
     }
     return TC_OK;
 }
@@ -831,6 +921,7 @@ extern "C" void tc_batch_destroy(tc_batch* bt) {
     cudaSetDevice(bt->device);
     if (bt->tables) cudaFree(bt->tables);
     if (bt->scratch) cudaFree(bt->scratch);
+    if (bt->err_dev) cudaFree(bt->err_dev);
     cudaSetDevice(cur);
     delete bt;
 }
@@ -872,7 +963,8 @@ extern "C" tc_status tc_mul(tc_ctx* ctx, const uint32_t* a, size_t na, const uin
     u32* rO = (u32*)(base + L.total + rows_bytes);
     CK(cudaMemsetAsync(rA, 0, pieces * lo * 4, st));
     CK(cudaMemcpyAsync(rA, longp, hi * 4, cudaMemcpyDeviceToDevice, st));
-    s = run_uniform(L, base, pieces, lo, rA, (long)lo, shortp, 0, rO, (long)(2 * lo), false, st, ctx);
+    s = run_uniform(L, base, pieces, lo, rA, (long)lo, shortp, 0, rO, (long)(2 * lo), false, st, ctx,
+                    ctx->err_dev);
     if (s) return s;
     CK(launch_overlap_add(rO, (long)(2 * lo), (int)(2 * lo), (int)pieces, (long)lo, out,
                           (long)(na + nb), st));

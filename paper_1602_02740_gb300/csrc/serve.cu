@@ -51,6 +51,7 @@ struct Group {
     cudaStream_t st = nullptr;
     cudaEvent_t done = nullptr;
     size_t bytes = 0;
+    int slot = -1;    // index of this group's bounded-wait error word in Server::err_host
 };
 
 struct Server {
@@ -72,6 +73,10 @@ struct Server {
     cudaStream_t streams[kStreams] = {};
     int rr = 0;
     cudaMemPool_t pool = nullptr;
+    // pinned host words, one per group in flight: each group's bounded-wait error
+    // word is copied here before its scratch is freed (worker thread only)
+    int* err_host = nullptr;
+    std::vector<int> free_slots;
     // statistics
     std::vector<double> lat_ms;
     double first_submit = -1, last_done = 0, bits = 0;
@@ -90,6 +95,7 @@ static size_t group_bytes(tc_ctx* ctx, size_t count, size_t s) {
 
 Server::~Server() {
     for (auto& kv : all) delete kv.second;
+    if (err_host) cudaFreeHost(err_host);
 }
 
 void Server::launch(std::vector<Request*>& reqs) {
@@ -110,7 +116,11 @@ void Server::launch(std::vector<Request*>& reqs) {
         const size_t c = g->reqs.size();
         const tc_opts o = plan_for(ctx, s);
         const BatchLayout L = layout_for(c, s, o, false);
-        g->bytes = L.total + 2 * align256(c * s * 4) + align256(c * 2 * s * 4);
+        const size_t rows_end = L.total + 2 * align256(c * s * 4) + align256(c * 2 * s * 4);
+        g->bytes = rows_end + 256;  // + the group's bounded-wait error word
+        g->slot = free_slots.back();
+        free_slots.pop_back();
+        err_host[g->slot] = 0;
         cudaError_t e = cudaEventCreateWithFlags(&g->done, cudaEventDisableTiming);
         void* scratch = nullptr;
         if (e == cudaSuccess) e = cudaMallocFromPoolAsync(&scratch, g->bytes, pool, g->st);
@@ -120,7 +130,9 @@ void Server::launch(std::vector<Request*>& reqs) {
             uint32_t* rA = (uint32_t*)(base + L.total);
             uint32_t* rB = (uint32_t*)(base + L.total + align256(c * s * 4));
             uint32_t* rO = (uint32_t*)(base + L.total + 2 * align256(c * s * 4));
+            int* err_dev = (int*)(base + rows_end);
             e = cudaMemsetAsync(rA, 0, 2 * align256(c * s * 4), g->st);
+            if (e == cudaSuccess) e = cudaMemsetAsync(err_dev, 0, sizeof(int), g->st);
             for (size_t k = 0; k < c && e == cudaSuccess; ++k) {
                 Request* r = g->reqs[k];
                 if (r->na) e = cudaMemcpyAsync(rA + k * s, r->a, r->na * 4, cudaMemcpyDeviceToDevice, g->st);
@@ -129,13 +141,16 @@ void Server::launch(std::vector<Request*>& reqs) {
             }
             if (e == cudaSuccess)
                 status = run_uniform(L, base, c, s, rA, (long)s, rB, (long)s, rO, (long)(2 * s), false,
-                                     g->st, nullptr);
+                                     g->st, nullptr, err_dev);
             for (size_t k = 0; k < c && e == cudaSuccess && status == TC_OK; ++k) {
                 Request* r = g->reqs[k];
                 if (r->na + r->nb)
                     e = cudaMemcpyAsync(r->out, rO + k * 2 * s, (r->na + r->nb) * 4,
                                         cudaMemcpyDeviceToDevice, g->st);
             }
+            if (e == cudaSuccess && status == TC_OK)
+                e = cudaMemcpyAsync(err_host + g->slot, err_dev, sizeof(int), cudaMemcpyDeviceToHost,
+                                    g->st);
             cudaError_t e2 = cudaFreeAsync(scratch, g->st);
             if (e == cudaSuccess) e = e2;
         }
@@ -149,6 +164,8 @@ void Server::launch(std::vector<Request*>& reqs) {
                 --slots_used;
             }
             if (g->done) cudaEventDestroy(g->done);
+            if (scratch || g->done) cudaStreamSynchronize(g->st);  // the slot may be in a copy
+            free_slots.push_back(g->slot);
             delete g;
         } else {
             inflight.push_back(g);
@@ -167,13 +184,14 @@ bool Server::poll_inflight() {
             continue;
         }
         const double t = now_s();
+        const bool timed_out = q == cudaSuccess && err_host[g->slot] != 0;
         {
             std::lock_guard<std::mutex> lk(mu);
             for (Request* r : g->reqs) {
-                r->state = q == cudaSuccess ? 2 : (int)tc_fail_cuda(q);
+                r->state = q != cudaSuccess ? (int)tc_fail_cuda(q) : timed_out ? (int)TC_ETIMEOUT : 2;
                 reserved -= r->need;
                 --slots_used;
-                if (q == cudaSuccess) {
+                if (q == cudaSuccess && !timed_out) {
                     lat_ms.push_back((t - r->t_submit) * 1e3);
                     bits += 32.0 * (double)(r->na + r->nb);
                     last_done = std::max(last_done, t);
@@ -181,6 +199,7 @@ bool Server::poll_inflight() {
             }
         }
         cudaEventDestroy(g->done);
+        free_slots.push_back(g->slot);
         delete g;
         inflight[i] = inflight.back();
         inflight.pop_back();
@@ -256,6 +275,12 @@ static Server* get_server_locked(tc_ctx* ctx, tc_status* st) {
             uint64_t keep = (uint64_t)ctx->budget;  // cache freed group scratch up to the budget
             e = cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep);
         }
+    }
+    if (e == cudaSuccess) {
+        // at most one group per admitted request is in flight
+        e = cudaHostAlloc(&s->err_host, Server::kMaxSlots * sizeof(int), cudaHostAllocDefault);
+        if (e == cudaSuccess)
+            for (int i = (int)Server::kMaxSlots - 1; i >= 0; --i) s->free_slots.push_back(i);
     }
     if (e != cudaSuccess) {
         *st = tc_fail_cuda(e);

@@ -20,6 +20,8 @@ struct BatchLayout {
     std::vector<LevelGeom> g;
     std::vector<long> P;          // products at each level (P[0] = count)
     std::vector<size_t> evalU, evalV, sgnU, sgnV, prod, work, evwork;
+    int base = TC_BASE_SCHOOLBOOK;
+    size_t ntt = 0;               // transform scratch of the base products (TC_BASE_NTT)
     size_t total = 0;
 };
 
@@ -29,9 +31,14 @@ BatchLayout layout_for(size_t count, size_t s, const tc_opts& o, bool square);
 
 // Run a uniform batch of `count` s x s products (operand rows A/Bm, result rows
 // OUT) with scratch `base` laid out by L.  ctx may be null (no phase timing).
+// Segment-parallel levels OR their bounded-wait error words into *sticky
+// (device memory; nullptr = not reported), by kernels on `st`: nothing waits.
 tc_status run_uniform(const BatchLayout& L, char* base, size_t count, size_t s, const uint32_t* A,
                       long lda, const uint32_t* Bm, long ldb, uint32_t* OUT, long ldo, bool square,
-                      cudaStream_t st, tc_ctx* ctx);
+                      cudaStream_t st, tc_ctx* ctx, int* sticky);
+
+// *sticky |= *word on `st` (one thread).
+cudaError_t launch_or_error(int* sticky, const int* word, cudaStream_t st);
 
 // Padded balanced length class of an operand length (at most 50% padding).
 size_t size_class(size_t L);
@@ -45,6 +52,13 @@ struct tc_ctx {
     void* aux = nullptr;        // staging buffers of the host-pointer entry point
     size_t aux_bytes = 0;
     std::vector<std::pair<size_t, tc_opts>> table;  // autotuned plans: (max limbs, plan)
+    int* err_dev = nullptr;     // sticky bounded-wait error word of this context's calls (tc_check)
+    // pinned staging of tc_mul_batch's index tables: two buffers used in turn, each
+    // reused only after the copy that last read it has completed (pin_ev)
+    void* pin[2] = {nullptr, nullptr};
+    size_t pin_bytes[2] = {0, 0};
+    cudaEvent_t pin_ev[2] = {nullptr, nullptr};
+    int pin_turn = 0;
     tc::Server* server = nullptr;
     // phase timing (tc_profile_enable)
     bool profile = false;

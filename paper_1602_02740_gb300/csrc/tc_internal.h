@@ -71,4 +71,11 @@ cudaError_t launch_overlap_add(const uint32_t* rows, long row_stride, int row_le
 
 cudaError_t launch_zero(uint32_t* p, size_t n, cudaStream_t st);
 
+// Base product by number-theoretic transform (ntt.cu): P products of s x s limbs.
+constexpr int NTT_MAX_LIMBS = 1 << 24;
+int ntt_log2(int s);
+size_t ntt_work_bytes(int s, long P, bool square);
+cudaError_t launch_ntt_mul(const uint32_t* A, long lda, const uint32_t* Bm, long ldb, uint32_t* OUT,
+                           long ldo, int s, long P, bool square, void* work, cudaStream_t st);
+
 }  // namespace tc

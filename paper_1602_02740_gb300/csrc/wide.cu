@@ -18,6 +18,8 @@
 #include <algorithm>
 #include <vector>
 
+#include "../../include/tc.h"
+#include "tc_ctx.h"
 #include "tc_device.cuh"
 #include "tc_internal.h"
 
@@ -69,12 +71,19 @@ __device__ __forceinline__ void st_rel(u64* p, u64 v) {
     asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
+// Failure-detection test settings of this device (tc_test_bounded_waits):
+// g_wait_polls > 0 replaces SPIN_LIMIT; g_withhold != 0 makes the first segment
+// of every add/subtract chain skip its publishes, so the waits behind it run out.
+__device__ int g_wait_polls = 0;
+__device__ int g_withhold = 0;
+
 // Wait (bounded) until status word *p is published; returns it.
 __device__ __forceinline__ u64 wait_status(const u64* p, int* err) {
     u64 v;
     int it = 0;
+    const int limit = g_wait_polls > 0 ? g_wait_polls : SPIN_LIMIT;
     while (((v = ld_acq(p)) & F_MASK) == 0) {
-        if (++it > SPIN_LIMIT) {
+        if (++it > limit) {
             atomicExch(err, 1);
             return F_INCL;  // give up: carry-in 0, result flagged invalid
         }
@@ -146,7 +155,8 @@ wide_addsub_kernel(WidePass wp, u64* status, int* counter, int* err) {
         u32 r[4];
         for (int pos = start; pos < end; pos += CH) addsub_chunk(C, X, Z, pos, carry, r, same);
         const u32 g = carry, pr = (!g && same) ? 1u : 0u;
-        if (lane_id() == 0) st_rel(st + seg, F_AGG | g | (pr << 1));
+        const bool publish = !(seg == 0 && g_withhold);
+        if (lane_id() == 0 && publish) st_rel(st + seg, F_AGG | g | (pr << 1));
         // look back
         u32 cin = 0;
         if (lane_id() == 0) {
@@ -156,7 +166,7 @@ wide_addsub_kernel(WidePass wp, u64* status, int* counter, int* err) {
                 if (v & 1u) { cin = 1; break; }          // generates
                 if (!(v & 2u)) { cin = 0; break; }       // kills
             }
-            st_rel(st + seg, F_INCL | (g | (pr & cin)));
+            if (publish) st_rel(st + seg, F_INCL | (g | (pr & cin)));
         }
         cin = __shfl_sync(FULL, cin, 0);
         // phase 2: with the true carry-in
@@ -820,3 +830,11 @@ cudaError_t launch_wide_interp(const LevelGeom& g, const u32* y, const uint8_t* 
 }
 
 }  // namespace tc
+
+extern "C" tc_status tc_test_bounded_waits(int polls, int withhold) {
+    if (polls < 0) return TC_EINVAL;
+    const int w = withhold ? 1 : 0;
+    cudaError_t e = cudaMemcpyToSymbol(tc::g_wait_polls, &polls, sizeof polls);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(tc::g_withhold, &w, sizeof w);
+    return e == cudaSuccess ? TC_OK : tc_fail_cuda(e);
+}

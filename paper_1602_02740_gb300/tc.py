@@ -33,19 +33,32 @@ class TCError(RuntimeError):
         super().__init__(f"{where}: {msg} (status {status}, cuda error {cuda})")
 
 
+TC_BASE_SCHOOLBOOK, TC_BASE_NTT = 0, 1
+
+
 class tc_opts(ctypes.Structure):
-    _fields_ = [("levels", ctypes.c_int), ("B", ctypes.c_int * TC_MAX_LEVELS)]
+    """A plan: B per Toom level, then the base product.  As a Python list a
+    plan is the B values, followed by "ntt" when the base product is the
+    number-theoretic transform (e.g. [16, "ntt"], or ["ntt"] alone)."""
+    _fields_ = [("levels", ctypes.c_int), ("B", ctypes.c_int * TC_MAX_LEVELS),
+                ("base", ctypes.c_int)]
 
     @classmethod
-    def of(cls, Bs: Sequence[int]) -> "tc_opts":
+    def of(cls, Bs: Sequence) -> "tc_opts":
         o = cls()
+        Bs = list(Bs)
+        o.base = TC_BASE_SCHOOLBOOK
+        if Bs and Bs[-1] == "ntt":
+            o.base = TC_BASE_NTT
+            Bs = Bs[:-1]
         o.levels = len(Bs)
         for i, B in enumerate(Bs):
             o.B[i] = int(B)
         return o
 
     def plan(self):
-        return [self.B[i] for i in range(self.levels)]
+        p = [self.B[i] for i in range(self.levels)]
+        return p + ["ntt"] if self.base == TC_BASE_NTT else p
 
 
 _vp, _sz, _u32p, _i64p, _u8p = (ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
@@ -55,6 +68,8 @@ _optp = ctypes.POINTER(tc_opts)
 _SIGS = {
     "tc_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, _sz, ctypes.c_char_p]),
     "tc_destroy": (None, [_vp]),
+    "tc_check": (ctypes.c_int, [_vp, _vp]),
+    "tc_test_bounded_waits": (ctypes.c_int, [ctypes.c_int, ctypes.c_int]),
     "tc_plan_for": (ctypes.c_int, [_vp, _sz, _optp]),
     "tc_scratch_bytes": (ctypes.c_int, [_vp, _sz, _sz, _optp, ctypes.POINTER(ctypes.c_size_t)]),
     "tc_mul": (ctypes.c_int, [_vp, _u32p, _sz, _u32p, _sz, _u32p, _optp, _vp]),
@@ -75,6 +90,9 @@ _SIGS = {
     "tc_pipe_wait": (ctypes.c_int, [_vp]),
     "tc_pipe_destroy": (None, [_vp]),
     "tc_schoolbook": (ctypes.c_int, [_sz, _sz, _u32p, _sz, _u32p, _sz, _u32p, _sz, _vp]),
+    "tc_ntt_mul": (ctypes.c_int, [_sz, _sz, _u32p, _sz, _u32p, _sz, _u32p, _sz, _vp, _vp]),
+    "tc_ntt_work_bytes": (ctypes.c_size_t, [_sz, _sz]),
+    "tc_ntt_root": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)]),
     "tc_toom_evaluate": (ctypes.c_int, [_sz, _sz, ctypes.c_int, _u32p, _sz, _u32p, _sz, _u8p, _vp]),
     "tc_toom_interpolate": (ctypes.c_int, [_sz, _sz, ctypes.c_int, _u32p, _sz, _u8p, _u8p, _u32p,
                                            _sz, _vp, _vp]),
@@ -185,6 +203,12 @@ def tc_create(device: int = 0, budget_bytes: int = 0, table: Optional[str] = Non
 
 def tc_destroy(ctx: Context):
     ctx.close()
+
+
+def tc_check(ctx: Context, stream=None):
+    """Wait for `stream`; raise TCError(TC_ETIMEOUT) if a bounded device wait of
+    a call on this context gave up since the last check."""
+    _check(lib().tc_check(ctx.handle, _stream(stream)), "tc_check")
 
 
 def tc_plan_for(ctx: Context, limbs: int):
@@ -358,6 +382,30 @@ def tc_schoolbook(A, B, OUT=None, stream=None):
     return OUT
 
 
+def tc_ntt_work_bytes(count: int, limbs: int) -> int:
+    return lib().tc_ntt_work_bytes(count, limbs)
+
+
+def tc_ntt_mul(A, B, OUT=None, work=None, stream=None):
+    """Row-wise products of 2-D (count, L) int32 device tensors by the transform
+    base product; OUT is (count, 2L).  `work`: device scratch (allocated if None)."""
+    import torch
+    count, L = A.shape
+    if OUT is None:
+        OUT = torch.empty((count, 2 * L), dtype=torch.int32, device=A.device)
+    if work is None:
+        work = torch.empty(max(1, tc_ntt_work_bytes(count, L)), dtype=torch.uint8, device=A.device)
+    _check(lib().tc_ntt_mul(count, L, _ptr(A), A.stride(0), _ptr(B), B.stride(0), _ptr(OUT),
+                            OUT.stride(0), _ptr(work), _stream(stream)), "tc_ntt_mul")
+    return OUT
+
+
+def tc_ntt_root(log2n: int) -> int:
+    r = ctypes.c_uint64()
+    _check(lib().tc_ntt_root(int(log2n), ctypes.byref(r)), "tc_ntt_root")
+    return r.value
+
+
 def level_sizes(limbs: int, B: int):
     """(b, e, estride, ystride) of one level, as the library lays it out."""
     n = B - 1
@@ -516,3 +564,9 @@ def tc_peak_madc(blocks: int, iters: int, sink, stream=None) -> float:
     _check(lib().tc_peak_madc(int(blocks), int(iters), _ptr(sink), _stream(stream),
                               ctypes.byref(n)), "tc_peak_madc")
     return n.value
+
+
+def tc_test_bounded_waits(polls: int, withhold: bool):
+    """Test hook: shorten the segment-parallel passes' bounded waits to `polls`
+    polls (0 = default) and, if `withhold`, make the waits run out."""
+    _check(lib().tc_test_bounded_waits(int(polls), 1 if withhold else 0), "tc_test_bounded_waits")

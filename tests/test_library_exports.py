@@ -99,3 +99,19 @@ def test_batch_tables_rejected_on_the_host(libtc):
         st = libtc.tc_batch_prepare(ctypes.addressof(fake_ctx), 2, p["a_off"], p["a_len"],
                                     p["b_off"], p["b_len"], p["o_off"], None, ctypes.byref(h))
         assert st == -1 and not h.value, (key, bad)
+
+
+def test_ntt_roots_of_unity(libtc):
+    """The transform's root for length 2^n has order exactly 2^n modulo
+    p = 2^64 - 2^32 + 1 (host-only entry point, no GPU)."""
+    p = (1 << 64) - (1 << 32) + 1
+    libtc.tc_ntt_root.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)]
+    for n in range(0, 33):
+        r = ctypes.c_uint64()
+        assert libtc.tc_ntt_root(n, ctypes.byref(r)) == 0
+        w = r.value
+        assert 0 < w < p
+        assert pow(w, 1 << n, p) == 1
+        if n:
+            assert pow(w, 1 << (n - 1), p) == p - 1     # primitive: half the order gives -1
+    assert libtc.tc_ntt_root(33, ctypes.byref(ctypes.c_uint64())) == -1
