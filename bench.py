@@ -374,7 +374,8 @@ def kernel_rooflines(phases, steps, ceiling, pk, pk_src):
 def large_products(ctx, tc, torch, stream):
     """Single products of 2^24, 2^26 and 2^27 bits: top-level B = 16 and 32
     (lower levels the cost model's best), products and squares, 5 timed calls
-    each; the library's own plan; the plain schoolbook at 2^24 bits.  Every
+    each; the library's own plan; the transform base product alone and the best
+    top-level B over it (Section 5); the plain schoolbook at 2^24 bits.  Every
     result is checked modulo three primes."""
     from paper_1602_02740_gb300 import autotune
     out = {}
@@ -388,6 +389,14 @@ def large_products(ctx, tc, torch, stream):
         for Btop in (16, 32):
             mine = [list(p) for p in allc if p and p[0] == Btop]
             plans[f"B{Btop}"] = min(mine, key=lambda p: autotune.model_seconds(L, p, 1))
+        plans["ntt"] = ["ntt"]
+        # Toom-Cook as the wrapper around the transform product (Section 5): best top B
+        best = None
+        for Btop in (2, 3, 4, 8, 16):
+            ms = _timed(torch, stream, lambda: tc.tc_mul(ctx, ga, gb, go, plan=[Btop, "ntt"]), 3)
+            if best is None or ms < best[0]:
+                best = (ms, [Btop, "ntt"])
+        plans["toom_over_ntt"] = best[1]
         for key, pl in plans.items():
             ms_m = _timed(torch, stream, lambda: tc.tc_mul(ctx, ga, gb, go, plan=pl), 5)
             ok_m = check_products(ha, hb, tc.to_numpy(go)[None])["ok"]
@@ -402,6 +411,20 @@ def large_products(ctx, tc, torch, stream):
                 "verified": check_products(ha, hb, tc.to_numpy(go)[None])["ok"]}
         out[f"2^{(L * 32).bit_length() - 1}_bits"] = entry
         del ga, gb, go
+    return out
+
+
+def ntt_batch_2e20(ctx, tc, torch, stream, dA, dB, dO, A, B, toom_value):
+    """The benchmark's batch through the transform base product alone and with
+    Toom-12 over it (Section 5), beside the Toom-Cook path's rate."""
+    P = dA.shape[0]
+    out = {}
+    for key, plan in (("ntt", ["ntt"]), ("toom12_over_ntt", [12, "ntt"])):
+        ms = _timed(torch, stream, lambda: tc.tc_mul_uniform(ctx, dA, dB, dO, plan=plan), 3)
+        rows = [0, P // 2, P - 1]
+        chk = check_products(A[rows], B[rows], tc.to_numpy(dO[rows]), exact_rows=(0,))
+        out[key] = {"plan": plan, "mults_per_s": P / (ms / 1e3), "ms_per_call": ms,
+                    "vs_toom_schoolbook": P / (ms / 1e3) / toom_value, "verified": chk["ok"]}
     return out
 
 
@@ -494,7 +517,8 @@ def serving(ctx, tc, count, rank, warm=2000):
     at once), then arrivals at 0.5x and 0.8x of it.  Latency = submit -> done."""
     import torch
     from paper_1602_02740_gb300 import inputs
-    sctx = tc.tc_create(torch.cuda.current_device(), budget_bytes=40 << 30)
+    sctx = tc.tc_create(torch.cuda.current_device(), budget_bytes=40 << 30,
+                        table=PLAN_TABLE if os.path.exists(PLAN_TABLE) else None)
     _, lens = inputs.poisson_stream(count, seed=5 + rank, rate_per_s=1.0)
     lens = lens.astype(np.int64)
     g = inputs.rng(9 + rank)
@@ -805,6 +829,7 @@ def main():
                                      "verified": chk["ok"]}
             del dA2
         other["plain_schoolbook_gpu_2e20"] = schoolbook_batch_2e20(ctx, tc, torch, stream, L, value)
+        other["ntt_2e20"] = ntt_batch_2e20(ctx, tc, torch, stream, dA, dB, dO, A, B, value)
 
     large = None
     if not args.no_large:

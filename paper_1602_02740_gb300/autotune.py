@@ -5,8 +5,10 @@ Candidates are all B sequences over {2, 3, 4, 5, 6, 8, 12, 16, 32} up to five
 levels whose base-case length falls in [LEAF_MIN, LEAF_MAX] limbs; a cost model
 (base-case limb products, interpolation work n^2 * values, evaluation work)
 ranks them and the best few are timed through the C ABI with CUDA events.
-The winners are written as a plan table (one line per size class:
-"<max_limbs> <levels> <B0> <B1> ...") that tc_create loads.
+From NTT_MIN limbs on, the transform base product alone and one or two Toom
+levels over it (Section 5) are timed as well.  The winners are written as a
+plan table (one line per size class: "<max_limbs> <levels> <B0> <B1> ...
+[ntt]") that tc_create loads.
 
     python -m paper_1602_02740_gb300.autotune --out paper_1602_02740_gb300/plans_gb300.txt
 """
@@ -30,6 +32,7 @@ LEAF_RATE = 6.9e12        # base-case limb products
 INTERP_RATE = 3.5e11      # n^2 x interpolation-value limbs
 EVAL_RATE = 1.3e12        # B x n x evaluation limbs
 LAUNCH_S = 6e-6           # per kernel launch
+NTT_MIN = 1024            # smallest size class at which transform-based plans are timed
 
 
 def level(s: int, B: int):
@@ -79,10 +82,27 @@ def candidates(s: int, max_levels: int = 5):
     return out
 
 
-def tune_size(ctx, s: int, count: int, top: int = 10, reps: int = 3, verbose=False):
+def ntt_candidates(s: int):
+    """Transform-based plans: the transform product alone, and one or two Toom
+    levels over it (Section 5)."""
+    if s < NTT_MIN:
+        return []
+    out = [("ntt",)]
+    for B in (2, 3, 4, 8, 16):
+        if B <= s:
+            out.append((B, "ntt"))
+    for B1, B2 in ((3, 3), (4, 4), (16, 4)):
+        if B1 * B2 <= s:
+            out.append((B1, B2, "ntt"))
+    return out
+
+
+def tune_size(ctx, s: int, count: int, top: int = 10, reps: int = 3, verbose=False, ntt=True):
     import torch
     from . import tc
     cands = sorted(candidates(s), key=lambda p: model_seconds(s, p, count))[:top]
+    if ntt:
+        cands += ntt_candidates(s)
     g = torch.Generator(device="cuda")
     g.manual_seed(s)
     A = torch.randint(-2 ** 31, 2 ** 31 - 1, (count, s), dtype=torch.int32, device="cuda", generator=g)
@@ -103,8 +123,9 @@ def tune_size(ctx, s: int, count: int, top: int = 10, reps: int = 3, verbose=Fal
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / reps
         if verbose:
-            print(f"  s={s} count={count} plan={list(plan)} {ms:.3f} ms "
-                  f"(model {model_seconds(s, plan, count) * 1e3:.3f})", flush=True)
+            model = ("" if plan and plan[-1] == "ntt"
+                     else f" (model {model_seconds(s, plan, count) * 1e3:.3f})")
+            print(f"  s={s} count={count} plan={list(plan)} {ms:.3f} ms{model}", flush=True)
         if best is None or ms < best[0]:
             best = (ms, list(plan))
     del A, B, O
@@ -127,6 +148,7 @@ def main():
     ap.add_argument("--work", type=float, default=2 ** 26, help="limbs per timed batch")
     ap.add_argument("--top", type=int, default=10)
     ap.add_argument("-v", action="store_true")
+    ap.add_argument("--no-ntt", action="store_true", help="schoolbook-base plans only")
     args = ap.parse_args()
     import torch
     from . import tc
@@ -136,7 +158,7 @@ def main():
     t0 = time.time()
     for s in size_classes(32, args.max_limbs):
         count = max(1, int(args.work // s))
-        best = tune_size(ctx, s, count, top=args.top, verbose=args.v)
+        best = tune_size(ctx, s, count, top=args.top, verbose=args.v, ntt=not args.no_ntt)
         if best is None:
             continue
         rows.append((s, best[1], best[0], count))
@@ -144,9 +166,12 @@ def main():
     with open(args.out, "w") as f:
         f.write("# plan table written by paper_1602_02740_gb300.autotune on "
                 f"{torch.cuda.get_device_name(0)}\n")
-        f.write("# <max_limbs> <levels> <B0> <B1> ...  (first row with max_limbs >= size wins)\n")
+        f.write("# <max_limbs> <levels> <B0> <B1> ... [ntt]  (first row with max_limbs >= size wins;\n"
+                "# ntt: the transform base product below the levels)\n")
         for s, plan, ms, count in rows:
-            f.write(f"{s} {len(plan)} {' '.join(map(str, plan))}\n")
+            Bs = [B for B in plan if B != "ntt"]
+            tail = " ntt" if plan and plan[-1] == "ntt" else ""
+            f.write(f"{s} {len(Bs)} {' '.join(map(str, Bs))}{tail}\n".replace("  ", " "))
     print(f"wrote {args.out} ({len(rows)} classes) in {time.time() - t0:.0f} s")
     ctx.close()
 

@@ -19,8 +19,10 @@ def _rows():
             line = line.strip()
             if not line or line.startswith("#"):
                 continue
-            nums = [int(x) for x in line.split()]
-            rows.append((nums[0], nums[1], nums[2:]))
+            words = line.split()
+            ntt = words[-1] == "ntt"
+            nums = [int(x) for x in (words[:-1] if ntt else words)]
+            rows.append((nums[0], nums[1], nums[2:] + (["ntt"] if ntt else [])))
     return rows
 
 
@@ -80,12 +82,16 @@ def test_plan_table_well_formed():
     assert sizes == sorted(sizes) and len(set(sizes)) == len(sizes)
     assert sizes[-1] >= 1 << 20  # covers the 2^20-bit workload (32768 limbs)
     for s, levels, plan in rows:
-        assert levels == len(plan) <= 5
+        ntt = bool(plan) and plan[-1] == "ntt"
+        Bs = plan[:-1] if ntt else plan
+        assert levels == len(Bs) <= 5
         L = s
-        for B in plan:
+        for B in Bs:
             assert B in at.BS and B <= L
             L = at.level(L, B)[1]
-        if plan:
+        if ntt:
+            assert s >= at.NTT_MIN and L <= 1 << 24, (s, plan, L)   # transform base product
+        elif Bs:
             assert at.LEAF_MIN <= L <= at.LEAF_MAX, (s, plan, L)
 
 
@@ -93,3 +99,12 @@ def test_plan_table_row_for_the_bench_size():
     # first row with max_limbs >= size wins
     row = next(r for r in _rows() if r[0] >= 32768)
     assert row[2] == [12, 6, 4]
+
+
+def test_ntt_candidates():
+    assert at.ntt_candidates(at.NTT_MIN - 1) == []
+    c = at.ntt_candidates(1 << 20)
+    assert ("ntt",) in c and all(p[-1] == "ntt" for p in c)
+    assert len(set(c)) == len(c)
+    for p in c:
+        assert all(B in at.BS for B in p[:-1])
