@@ -864,6 +864,8 @@ def main():
                        "l2": f"operands ({2 * P * L * 4 / 1e6:.0f} MB) exceed the 129 MB L2; no flush"},
             "verified": verified,
             "roofline": roof, "rooflines": roofs, "int_ceiling": ceiling,
+            "phases": [{"kind": p["kind"], "level": p["level"], "kernel": p["kernel"],
+                        "ms_per_step": p["ms"] / args.steps} for p in phases],
             "sweep": sweep, "mixed_batch": mixed, "serving": serve, "configs": other,
             "large": large, "cpu_baseline": cpu, "cpu_baselines": cpus, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk,

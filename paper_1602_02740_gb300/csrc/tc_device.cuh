@@ -380,6 +380,24 @@ __device__ __forceinline__ void warp_sub_seg(const u32 a[KL], const u32 b[KL], u
     borrow = bout;
 }
 
+// Two independent warp subtractions, interleaved step by step (more
+// independent instructions between the ballots of each).
+template <int KL>
+__device__ __forceinline__ void warp_sub_seg2(const u32 a0[KL], const u32 b0[KL], u32& bor0, u32 r0[KL],
+                                              const u32 a1[KL], const u32 b1[KL], u32& bor1, u32 r1[KL]) {
+    const u32 g0 = sub_seg<KL>(a0, b0, 0u, r0);
+    const u32 g1 = sub_seg<KL>(a1, b1, 0u, r1);
+    const bool p0 = !g0 && zero_seg<KL>(r0);
+    const bool p1 = !g1 && zero_seg<KL>(r1);
+    u32 o0, o1;
+    const u32 c0 = warp_carry_scan(g0 != 0u, p0, bor0, &o0);
+    const u32 c1 = warp_carry_scan(g1 != 0u, p1, bor1, &o1);
+    dec_seg<KL>(r0, c0);
+    dec_seg<KL>(r1, c1);
+    bor0 = o0;
+    bor1 = o1;
+}
+
 // Exact division of a warp chunk of 32 KL limbs by dc.d (constants built for this KL).
 // x mod d for x < 2^32, d odd (q below is floor(x / d) or at most two less).
 __device__ __forceinline__ u32 mod_small(u32 x, u32 d, u32 recip) {

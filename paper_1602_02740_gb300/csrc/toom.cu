@@ -1478,6 +1478,380 @@ static FinTable make_fin_table(int n, int KL) {
 }
 
 // ---------------------------------------------------------------------------
+// Streaming interpolation with the two polynomials on two warps.
+//
+// After the even-odd combine (Section 4) the even polynomial (values ce) and
+// the odd one (co) go through Theorems 3.2 and 3.3 independently, so each
+// product gets a pair of warps: warp 2q+0 streams ce, warp 2q+1 streams co.
+// Both read the pointwise products and form their own half of the combine
+// (the even warp S = W(x) +- |W(-x)|, the odd warp T = W(x) -+ |W(-x)|).  A
+// warp keeps one polynomial's n + 1 value windows, so its shared memory is
+// about half of the one-warp design and twice as many products are resident.
+//
+// The same windows as interp_stream_kernel, with these differences: every
+// stage emits its window one limb lower (a right shift by R < 32 bits reads
+// the limb above, so one limb of look-behind per chain suffices), hence c_m is
+// final at offset m + 1; chain borrows are packed one bit per chain; the
+// deferred divisions are the same (FinTable, one word per slot).  After the
+// Theorem 3.3 pass both warps of a block meet at a barrier and the even warp
+// recomposes the product from the work buffer.
+// ---------------------------------------------------------------------------
+struct SplitLayout {
+    int vals, st0, st1, stb, stm, stf, words;
+};
+
+__host__ __device__ inline SplitLayout split_layout(int n, int C, int fin_slots) {
+    SplitLayout L;
+    const int chains = n * (n + 1) / 2;
+    L.vals = (n + 1) * C;
+    L.st0 = 3 * (n + 1);          // combine: carry or borrow, up to two look-behind limbs
+    L.st1 = chains;               // one look-behind limb per chain (loop 1; loop 2 reuses it)
+    L.stb = (chains + 31) / 32;   // chain borrows, one bit per chain
+    L.stm = 4 * (n + 1);          // deferred multiplications: (hi, carry) per factor
+    L.stf = fin_slots;            // deferred divisions: one borrow per divisor
+    const int w = L.vals + L.st0 + L.st1 + L.stb + L.stm + L.stf;
+    L.words = (w + 3) / 4 * 4;    // the next warp's windows stay 16-byte aligned
+    return L;
+}
+
+// Store this lane's KL limbs of a window starting at absolute limb `start`
+// (any parity) into a row of Y limbs, dropping limbs outside [0, Y).
+template <int KL>
+__device__ __forceinline__ void st_window_any(u32* row, int start, int Y, const u32 v[KL]) {
+    const int p0 = start + KL * lane_id();
+    if ((start & 1) == 0) {
+#pragma unroll
+        for (int j = 0; j < KL; j += 2) {
+            const int q = p0 + j;
+            if (q >= 0 && q + 2 <= Y) *reinterpret_cast<uint2*>(row + q) = make_uint2(v[j], v[j + 1]);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < KL; ++j) {
+            const int q = p0 + j;
+            if (q >= 0 && q < Y) row[q] = v[j];
+        }
+    }
+}
+
+__device__ __forceinline__ u32 get_bit(const u32* words, int t) { return (words[t >> 5] >> (t & 31)) & 1u; }
+
+template <int KL, int MINB>
+__global__ void __launch_bounds__(256, MINB)
+interp_split_kernel(InterpArgs a, DivTable dt, FinTable ft, long P) {
+    constexpr int C = 32 * KL;
+    extern __shared__ __align__(16) u32 sm[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int p = warp & 1;  // 0: even polynomial, 1: odd polynomial
+    const long k = (long)blockIdx.x * (blockDim.x >> 6) + (warp >> 1);
+    const bool active = k < P;  // every warp reaches the block barrier below
+    const LevelGeom& g = a.g;
+    const int n = g.n, Y = g.Y, len = 2 * g.e;
+    const int npts = 2 * g.B - 1;
+    const SplitLayout L = split_layout(n, C, ft.off[n + 1]);
+    u32* vals = sm + (long)warp * L.words;
+    u32* st0 = vals + L.vals;
+    u32* st1 = st0 + L.st0;
+    u32* stb = st1 + L.st1;
+    u32* stm = stb + L.stb;
+    u32* stf = stm + L.stm;
+    u32* W = a.work + (active ? k : 0) * (long)(2 * (n + 1)) * Y;
+    auto V = [&](int m) -> u32* { return vals + m * C + KL * lane; };
+    auto Wrow = [&](int pp, int m) -> u32* { return W + (long)(pp * (n + 1) + m) * Y; };
+    auto ldv = [&](const u32* q, u32 v[KL]) { ld_seg<KL>(q, v); };
+    auto set_bit = [&](u32* words, int t, u32 b) {  // lane 0 only
+        const u32 m = 1u << (t & 31);
+        words[t >> 5] = b ? (words[t >> 5] | m) : (words[t >> 5] & ~m);
+    };
+    if (active) {
+        const u32* yk = a.y + k * npts * (long)g.ystride;
+        u32 negmask = 0;  // bit m: |W(-2^(m-1))| was negated
+        for (int m = 1; m <= n; ++m) {
+            bool sg = false;
+            if (a.su) sg ^= a.su[k * npts + 2 * m] != 0;
+            if (a.sv) sg ^= a.sv[k * npts + 2 * m] != 0;
+            negmask |= sg ? 1u << m : 0u;
+        }
+        for (int i = lane; i < L.st0 + L.st1 + L.stb + L.stm + L.stf; i += 32) st0[i] = 0;
+        __syncwarp();
+
+        // ---- pass A: even-odd combine and Newton loop 1 ----
+        const int grow = (n * (n - 1) + 31) / 32 + 1;  // limbs of the deferred scale factors
+        const int stepsA = (Y + 2 * n + 2 + grow + C - 1) / C;
+        for (int step = 0; step < stepsA; ++step) {
+            const int base = C * step;
+            __syncwarp();
+            if (p == 0) {  // node 0: ce_0 = y_0, one limb lower
+                u32 y0[KL], e[KL + 1], o[KL];
+                const u32 h[1] = {st0[1]};
+                ld_seg_masked<KL>(yk, base + KL * lane, len, y0);
+                look_behind<KL, 1>(y0, h, e);
+#pragma unroll
+                for (int j = 0; j < KL; ++j) o[j] = e[j];
+                st_seg<KL>(V(0), o);
+                __syncwarp();
+                if (lane == 31) st0[1] = y0[KL - 1];
+                st_window_any<KL>(Wrow(0, 0), base - 1, Y, o);
+            }
+            // eq. 4.5-4.6, x = 2^(m-1): the even warp forms S = neg ? D : A and
+            // ce_m = S / 2; the odd warp T = neg ? A : D and co_m = x T / 2, where
+            // A = W(x) + |W(-x)|, D = W(x) - |W(-x)|; the next node's rows load
+            // while this node is combined
+            u32 pn[KL], qn[KL];
+            ld_seg_masked<KL>(yk + (long)g.ystride, base + KL * lane, len, pn);
+            ld_seg_masked<KL>(yk + 2 * (long)g.ystride, base + KL * lane, len, qn);
+            for (int m = 1; m <= n; ++m) {
+                u32* s = st0 + 3 * m;
+                const bool neg = (negmask >> m) & 1u;
+                u32 pv[KL], qv[KL], r[KL], out[KL];
+#pragma unroll
+                for (int j = 0; j < KL; ++j) { pv[j] = pn[j]; qv[j] = qn[j]; }
+                if (m < n) {
+                    ld_seg_masked<KL>(yk + (2 * m + 1) * (long)g.ystride, base + KL * lane, len, pn);
+                    ld_seg_masked<KL>(yk + (2 * m + 2) * (long)g.ystride, base + KL * lane, len, qn);
+                }
+                u32 cb = s[0];
+                if ((p == 0) != neg) warp_add_seg<KL>(pv, qv, cb, r);
+                else warp_sub_seg<KL>(pv, qv, cb, r);
+                const bool right = p == 0 || m == 1;  // / 2 (else a left shift by m - 2)
+                if (right) {
+                    u32 e[KL + 1];
+                    const u32 h[1] = {s[2]};
+                    look_behind<KL, 1>(r, h, e);
+#pragma unroll
+                    for (int j = 0; j < KL; ++j) out[j] = fshr(e[j], e[j + 1], 1);
+                } else {
+                    u32 e[KL + 2];
+                    const u32 h[2] = {s[1], s[2]};
+                    look_behind<KL, 2>(r, h, e);
+#pragma unroll
+                    for (int j = 0; j < KL; ++j) out[j] = fshl(e[j], e[j + 1], (u32)(m - 2));
+                }
+                st_seg<KL>(V(m), out);
+                __syncwarp();
+                if (lane == 0) s[0] = cb;
+                if (lane == 31) { s[1] = r[KL - 2]; s[2] = r[KL - 1]; }
+            }
+            // Theorem 3.2 on the scaled values, in place with m descending (each
+            // update reads the old c'_(m-1)); the odd polynomial's c_0 is 0.  The
+            // chains of a stage are independent, so they run in pairs (m, m - 1).
+            int t1 = 0;  // chain index of (kk, kk)
+            for (int kk = 1; kk <= n; ++kk) {
+                for (int m = n; m >= kk; m -= 2) {
+                    const bool two = m - 1 >= kk;          // warp-uniform
+                    const int mb = m - 1;
+                    const int ta = t1 + m - kk, tb = ta - 1;
+                    const u32 Ra = (u32)(m == kk ? 2 * (m - 1) : 2 * (m - kk - 1));
+                    const u32 Rb = (u32)(mb == kk ? 2 * (mb - 1) : 2 * (mb - kk - 1));
+                    // the chain (kk, kk) scales c'_(kk-1) by d_(kk-1) = f1 f2 first
+                    const bool scale = (two ? mb : m) == kk && kk >= 2;
+                    const u32 f1 = scale ? dt.d[0][kk - 1].d : 1u;
+                    const u32 f2 = scale ? dt.d[1][kk - 1].d : 1u;
+                    u32* sm4 = stm + 4 * kk;
+                    u32 xa[KL], za[KL], zb[KL], ms[4];
+#pragma unroll
+                    for (int j = 0; j < KL; ++j) { za[j] = 0; zb[j] = 0; }
+                    ldv(V(m), xa);
+                    if (m > 1 || p == 0) ldv(V(m - 1), za);   // also chain b's x
+                    if (two && (mb > 1 || p == 0)) ldv(V(mb - 1), zb);
+                    if (f1 > 1) {
+                        u32* zs = two ? zb : za;
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) ms[i] = sm4[i];
+                        u32 zz[KL];
+                        warp_mul_small<KL>(zs, f1, ms[0], ms[1], zz);
+#pragma unroll
+                        for (int j = 0; j < KL; ++j) zs[j] = zz[j];
+                        if (f2 > 1) {
+                            warp_mul_small<KL>(zs, f2, ms[2], ms[3], zz);
+#pragma unroll
+                            for (int j = 0; j < KL; ++j) zs[j] = zz[j];
+                        }
+                    }
+                    u32 bwa = get_bit(stb, ta), bwb = two ? get_bit(stb, tb) : 0u;
+                    u32 dva[KL], dvb[KL], ea[KL + 1], eb[KL + 1], oa[KL], ob[KL];
+                    const u32 ha[1] = {st1[ta]};
+                    if (two) {
+                        const u32 hb[1] = {st1[tb]};
+                        // chain b: x = old c'_(m-1) = za (before any scaling of chain a: none)
+                        u32 xb[KL];
+#pragma unroll
+                        for (int j = 0; j < KL; ++j) xb[j] = za[j];
+                        warp_sub_seg2<KL>(xa, za, bwa, dva, xb, zb, bwb, dvb);
+                        look_behind<KL, 1>(dva, ha, ea);
+                        look_behind<KL, 1>(dvb, hb, eb);
+#pragma unroll
+                        for (int j = 0; j < KL; ++j) {
+                            oa[j] = fshr(ea[j], ea[j + 1], Ra);
+                            ob[j] = fshr(eb[j], eb[j + 1], Rb);
+                        }
+                        st_seg<KL>(V(m), oa);
+                        st_seg<KL>(V(mb), ob);
+                    } else {
+                        warp_sub_seg<KL>(xa, za, bwa, dva);
+                        look_behind<KL, 1>(dva, ha, ea);
+#pragma unroll
+                        for (int j = 0; j < KL; ++j) oa[j] = fshr(ea[j], ea[j + 1], Ra);
+                        st_seg<KL>(V(m), oa);
+                    }
+                    __syncwarp();
+                    if (lane == 0) {
+                        set_bit(stb, ta, bwa);
+                        if (two) set_bit(stb, tb, bwb);
+                        if (f1 > 1) {
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) sm4[i] = ms[i];
+                        }
+                    }
+                    if (lane == 31) {
+                        st1[ta] = dva[KL - 1];
+                        if (two) st1[tb] = dvb[KL - 1];
+                    }
+                    __syncwarp();
+                }
+                t1 += n - kk + 1;
+                // c'_kk is final, at offset kk + 1: divide by d_1 ... d_(kk-1) and store
+                u32 v[KL];
+                ldv(V(kk), v);
+                u32* sf = stf + ft.off[kk];
+                const int nf = ft.nfull[kk] + ft.haspart[kk];
+                for (int i = 0; i < nf; ++i) {
+                    const DivConst& dc = i < ft.nfull[kk] ? ft.full[i] : ft.part[kk];
+                    u32 B = sf[i];
+                    warp_exact_div_seg<KL>(v, dc, B);
+                    __syncwarp();
+                    if (lane == 0) sf[i] = B;
+                }
+                st_window_any<KL>(Wrow(p, kk), base - kk - 1, Y, v);
+            }
+        }
+        __syncwarp();
+        for (int i = lane; i < L.st1 + L.stb; i += 32) st1[i] = 0;
+        __syncwarp();
+
+        // ---- pass B: Newton to monomial basis (Theorem 3.3), aligned windows ----
+        for (int base = 0; base < Y; base += C) {
+            __syncwarp();
+            for (int m = 1; m <= n; ++m)
+#pragma unroll
+                for (int j = 0; j < KL; j += 4) cp_async16(V(m) + j, Wrow(p, m) + base + KL * lane + j);
+            cp_async_wait_all();
+            __syncwarp();
+            int t2 = 0;  // chain index of (m, m)
+            for (int m = n - 1; m >= 1; --m) {
+                const u32 S = (u32)(2 * (m - 1));
+                // in place, kx ascending: each chain reads the old c_(kx+1); the chains
+                // of a stage are independent and run in pairs (kx, kx + 1)
+                for (int kx = m; kx <= n - 1; kx += 2) {
+                    const bool two = kx + 1 <= n - 1;  // warp-uniform
+                    const int ta = t2 + kx - m, tb = ta + 1;
+                    u32 xa[KL], za[KL], zb[KL], ea[KL + 1], eb[KL + 1], sa[KL], sb[KL], ra[KL], rb[KL];
+                    ldv(V(kx), xa);
+                    ldv(V(kx + 1), za);                // also chain b's x
+                    u32 bwa = get_bit(stb, ta), bwb = two ? get_bit(stb, tb) : 0u;
+                    const u32 ha[1] = {st1[ta]};
+                    look_behind<KL, 1>(za, ha, ea);
+#pragma unroll
+                    for (int j = 0; j < KL; ++j) sa[j] = fshl(ea[j], ea[j + 1], S);
+                    if (two) {
+                        ldv(V(kx + 2), zb);
+                        const u32 hb[1] = {st1[tb]};
+                        look_behind<KL, 1>(zb, hb, eb);
+#pragma unroll
+                        for (int j = 0; j < KL; ++j) sb[j] = fshl(eb[j], eb[j + 1], S);
+                        warp_sub_seg2<KL>(xa, sa, bwa, ra, za, sb, bwb, rb);
+                        st_seg<KL>(V(kx), ra);
+                        st_seg<KL>(V(kx + 1), rb);
+                    } else {
+                        warp_sub_seg<KL>(xa, sa, bwa, ra);
+                        st_seg<KL>(V(kx), ra);
+                    }
+                    __syncwarp();
+                    if (lane == 0) {
+                        set_bit(stb, ta, bwa);
+                        if (two) set_bit(stb, tb, bwb);
+                    }
+                    if (lane == 31) {
+                        st1[ta] = za[KL - 1];
+                        if (two) st1[tb] = zb[KL - 1];
+                    }
+                    __syncwarp();
+                }
+                t2 += n - m;
+            }
+            for (int m = 1; m <= n - 1; ++m) {
+                u32 v[KL];
+                ldv(V(m), v);
+                st_seg<KL>(Wrow(p, m) + base + KL * lane, v);
+            }
+        }
+    }
+    __syncthreads();  // both polynomials of every product of the block are in the work buffer
+    if (!active || p != 0) return;
+
+    // ---- pass C: recompose out[l] = sum_t w_t[l - t b], w_2i = ce_i, w_2i+1 = co_(i+1) ----
+    u32* out = a.out + k * a.out_stride;
+    const bool aligned = ((reinterpret_cast<uintptr_t>(out) & 15u) == 0);
+    UnsignedNorm nst{0, 0};
+    const int nterms = 2 * n + 1;
+    auto load_term = [&](int l0, int tt, u32 q[4]) {
+        const int x = l0 - tt * g.b;
+        const u32* w = Wrow(tt & 1, (tt + 1) >> 1);
+        if (x >= 0 && x + 4 <= Y && ((x & 3) == 0)) {
+            const uint4 v = ld4(w + x);
+            q[0] = v.x; q[1] = v.y; q[2] = v.z; q[3] = v.w;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) q[j] = x + j >= 0 && x + j < Y ? w[x + j] : 0u;
+        }
+    };
+    auto issue = [&](int l0, u32 q[4][4], int& trest) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) q[i][j] = 0;
+        trest = -1;
+        if (l0 >= a.out_len) return;
+        int t = (l0 + 3) / g.b;
+        if (t > nterms - 1) t = nterms - 1;
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            if (t - i >= 0 && l0 - (t - i) * g.b < Y) load_term(l0, t - i, q[i]);
+        trest = t - 4;
+    };
+    u32 qn[4][4];
+    int tn;
+    issue(4 * lane, qn, tn);
+    for (int base_l = 0; base_l < a.out_len; base_l += CH) {
+        u64 cols[4] = {0, 0, 0, 0};
+        const int l0 = base_l + 4 * lane;
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) cols[j] += qn[i][j];
+        for (int t = tn; t >= 0 && l0 - t * g.b < Y; --t) {
+            u32 r[4];
+            load_term(l0, t, r);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) cols[j] += r[j];
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (l0 + j >= a.out_len) cols[j] = 0;
+        issue(l0 + CH, qn, tn);
+        u32 d[4];
+        warp_norm_unsigned(cols, nst, d);
+        if (aligned && l0 + 4 <= a.out_len) {
+            st4(out + l0, d);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (l0 + j < a.out_len) out[l0 + j] = d[j];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Register-resident warp-per-product interpolation for short values
 // (Y <= 32 KL, degree n small): each lane holds KL limbs of every value, so a
 // whole value is one warp chunk and every chain of Section 4 / Theorems 3.2
@@ -1743,6 +2117,31 @@ cudaError_t launch_interp(const LevelGeom& g, const u32* y, const uint8_t* su, c
                 for (int nn = 1; nn < 32; ++nn) fins[nn] = make_fin_table(nn, 4);
             });
             const FinTable& ft = fins[g.n];
+            if (g.n >= 8 && g.n <= 15 && g.Y % 256 == 0) {
+                // two warps per product (one per polynomial), four products per block,
+                // windows of 256 limbs (8 per lane; Y is a multiple of 256).  Only for
+                // high degree: there the one-warp kernel's windows of both polynomials
+                // limit it to 16 resident warps per SM; at low degree it already holds 32
+                // and the split kernel's duplicated combine makes it slower
+                static FinTable fins8[32];
+                static std::once_flag fin8_once;
+                std::call_once(fin8_once, [] {
+                    for (int nn = 1; nn < 32; ++nn) fins8[nn] = make_fin_table(nn, 8);
+                });
+                const FinTable& ft8 = fins8[g.n];
+                const int split_warp = split_layout(g.n, 256, ft8.off[g.n + 1]).words * 4;
+                const size_t smem = (size_t)8 * split_warp;
+                if (smem <= (size_t)STREAM_SMEM_MAX) {
+                    static std::once_flag split_once;
+                    std::call_once(split_once, [] {
+                        cudaFuncSetAttribute(interp_split_kernel<8, 2>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, STREAM_SMEM_MAX);
+                    });
+                    note_kernel("interp_split_kernel<8>");
+                    interp_split_kernel<8, 2><<<(unsigned)((P + 3) / 4), 256, smem, st>>>(a, dt8, ft8, P);
+                    return cudaGetLastError();
+                }
+            }
             const int per_warp = stream_layout(g.n, 128, ft.off[g.n + 1]).words * 4;
             // registers per warp as allocated (per thread rounded up to 8)
             static int regs_per_warp = 0;

@@ -479,7 +479,9 @@ def test_square_lane_kernel(tc, L):
 @pytest.mark.parametrize("B,L", [(2, 9), (3, 100), (4, 259), (8, 130), (3, 2), (4, 2000), (8, 2055),
                                  (12, 6000), (20, 4000), (32, 3000),
                                  (2, 5000), (3, 4000), (6, 3000), (7, 4000), (10, 3000),
-                                 (3, 450), (3, 650), (2, 400), (4, 600), (6, 500), (5, 400)])
+                                 (3, 450), (3, 650), (2, 400), (4, 600), (6, 500), (5, 400),
+                                 # two warps per product (degree 8..15, values a multiple of 256 limbs)
+                                 (9, 3000), (16, 8000)])
 def test_interpolate_many_products(tc, B, L):
     import torch
     count = 2100
