@@ -72,7 +72,7 @@ def parse():
                    help="skip the Toom-3 at 1024 limbs and the all-ones / sparse 2^20-bit lines")
     p.add_argument("--no-large", action="store_true",
                    help="skip the single products of 2^24, 2^26 and 2^27 bits")
-    p.add_argument("--case", choices=["interp", "leaf", "eval"], default=None,
+    p.add_argument("--case", choices=["interp", "leaf", "eval", "ntt"], default=None,
                    help="time one kernel call for a profiler capture instead of the benchmark")
     p.add_argument("--count", type=int, default=None, help="--case: products or rows")
     p.add_argument("--B", type=int, default=12, help="--case interp/eval: blocks")
@@ -614,6 +614,7 @@ def run_case(args):
             pointwise products (evaluation, then products of the evaluations).
     leaf:   the batched schoolbook (tc_schoolbook) of `count` products.
     eval:   one level's evaluation (tc_toom_evaluate) of `count` operands.
+    ntt:    the transform base product (tc_ntt_mul) of `count` products.
     Prints one JSON line with the mean time of `reps` calls after one untimed call.
     """
     import torch
@@ -625,6 +626,12 @@ def run_case(args):
         A, B = _rand_dev(torch, (count, L), 1), _rand_dev(torch, (count, L), 2)
         OUT = torch.empty((count, 2 * L), dtype=torch.int32, device="cuda")
         ms = _time_case(torch, lambda: tc.tc_schoolbook(A, B, OUT), args.reps)
+    elif args.case == "ntt":
+        count, L = args.count or 1, args.limbs
+        A, B = _rand_dev(torch, (count, L), 1), _rand_dev(torch, (count, L), 2)
+        OUT = torch.empty((count, 2 * L), dtype=torch.int32, device="cuda")
+        work = torch.empty(tc.tc_ntt_work_bytes(count, L), dtype=torch.uint8, device="cuda")
+        ms = _time_case(torch, lambda: tc.tc_ntt_mul(A, B, OUT, work), args.reps)
     elif args.case == "eval":
         count, L = args.count or 2432, args.limbs
         U = _rand_dev(torch, (count, L), 1)

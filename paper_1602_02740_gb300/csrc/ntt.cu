@@ -13,12 +13,15 @@
 // the digit vectors is the exact digit-wise product, because every coefficient
 // is below N (2^16 - 1)^2 < 2^(n + 32) < p for n <= 31.  The transform is a
 // four-step decomposition over fields of the point index (at most 8 bits,
-// 256 points, per pass): each pass runs, for every column of a block, an
-// in-place radix-2 transform of one field in shared memory and multiplies the
-// results by the four-step twiddles.  Forward passes go from the top field
-// down and leave the spectrum in a fixed permuted order; the inverse passes
-// undo them in reverse order, so no reordering pass is needed.  The
-// coefficients c_k are then placed at bit 16k and carried into 2s limbs.
+// 256 points, per pass): each pass runs, for every column of a block, a
+// radix-2 transform of one field (staged in shared memory, its stages in
+// registers) and multiplies the results by the four-step twiddles.  Forward
+// passes go from the top field down and leave the spectrum in a fixed permuted
+// order; the inverse passes undo them in reverse order, so no reordering pass
+// is needed.  The first forward pass reads the digits straight from the limbs
+// and the second operand's last forward pass multiplies by the first
+// operand's spectrum (the pointwise product).  The coefficients c_k are then
+// placed at bit 16k and carried into 2s limbs.
 #include <algorithm>
 #include <map>
 #include <mutex>
@@ -144,39 +147,52 @@ static cudaError_t ntt_tables(int n, NttTables* out) {
 struct NttPassArgs {
     u64* X;          // the whole batch: P transforms of N points, back to back
     long cols;       // columns of the pass over the batch: P N / R
-    int n, m, k;     // N = 2^n; blocks of M = 2^m points; R = 2^k-point sub-transforms
+    int n, m;        // N = 2^n; blocks of M = 2^m points
     const u64* tlo;  // two-level table of w^x (w = the N-th root, or its inverse)
     const u64* thi;
     int h;
+    // optional fusions
+    const u32* limbs;  // first forward pass: points are the 16-bit digits of these rows
+    long lda;
+    int s;             // limbs per row (digits 2s, zero beyond)
+    const u64* mulby;  // last forward pass: outputs multiplied by mulby[pos] and by ninv
+    int square;        // last forward pass: outputs squared and multiplied by ninv
+    u64 ninv;
 };
 
 __device__ __forceinline__ u64 root_pow(const NttPassArgs& a, unsigned x) {
     return gl_mul(a.thi[x >> a.h], a.tlo[x & ((1u << a.h) - 1)]);
 }
 
-// One pass: for each column (block Bg, column sigma) the R points
+// One pass: for each column (block Bg, column sigma) the R = 2^K points
 // Bg M + r S + sigma (S = M / R) are transformed along r.  Forward: radix-2
-// decimation in frequency (result for frequency kappa at r = bitrev(kappa)),
+// decimation in frequency (the result for frequency kappa at r = bitrev(kappa)),
 // then the point at (r, sigma) is multiplied by w_M^(sigma kappa).  Inverse:
 // multiplied by w_M^(-sigma kappa) first, then radix-2 decimation in time back
-// to natural order (the sub-transform's factor R is removed by N^-1 later).
-template <bool INV>
+// to natural order (the factor R is removed by N^-1 at the pointwise product).
+// The tile (4096 points: R rows x C columns) is staged in shared memory; each
+// thread runs the stages of one half of the index bits in registers: round 1
+// the high stages on groups of 2^K1 points strided by 2^K2, round 2 the low
+// stages on groups of 2^K2 consecutive points (K = K1 + K2).
+template <bool INV, int K>
 __global__ void __launch_bounds__(NTT_THREADS)
 ntt_pass_kernel(NttPassArgs a) {
-    extern __shared__ u64 sm[];
-    const int R = 1 << a.k, C = NTT_TILE >> a.k, pitch = C + 1;
-    const int ms = a.m - a.k;                     // log2 S
+    constexpr int R = 1 << K, C = NTT_TILE >> K, PITCH = C + 1;
+    constexpr int K1 = (K + 1) / 2, K2 = K / 2;
+    constexpr int G1 = 1 << K1, G2 = 1 << K2;
+    constexpr int NG1 = NTT_TILE / G1 / NTT_THREADS, NG2 = NTT_TILE / G2 / NTT_THREADS;
+    __shared__ u64 wr[R / 2 > 0 ? R / 2 : 1];   // w_R^t, t < R / 2 (forward or inverse)
+    extern __shared__ u64 sx[];                  // [R][PITCH]
+    const int ms = a.m - K;                      // log2 S
     const long S = 1L << ms;
-    u64* wr = sm;                                 // w_R^t, t < R / 2 (forward or inverse)
-    u64* sx = sm + (R / 2 > 0 ? R / 2 : 1);       // [R][pitch]
     const long gc0 = (long)blockIdx.x * C;
     const int tid = threadIdx.x;
-    const unsigned rstep = 1u << (a.n - a.k);     // w_R = w^(N/R)
+    const unsigned rstep = 1u << (a.n - K);      // w_R = w^(N/R)
     for (int t = tid; t < R / 2; t += NTT_THREADS) wr[t] = root_pow(a, (unsigned)t * rstep);
-    // load the tile, coalesced: C consecutive columns of one block (S >= C), or
-    // C / S whole consecutive blocks (S < C)
-    for (int idx = tid; idx < NTT_TILE; idx += NTT_THREADS) {
-        int r, c;
+    const long N = 1L << a.n;
+    // coalesced tile order: C consecutive columns of one block (S >= C), or C / S
+    // whole consecutive blocks (S < C)
+    auto tile_rc = [&](int idx, int& r, int& c) {
         if (S >= C) {
             r = idx / C;
             c = idx - r * C;
@@ -185,102 +201,141 @@ ntt_pass_kernel(NttPassArgs a) {
             r = rem >> ms;
             c = blk * (int)S + (rem & (int)(S - 1));
         }
+    };
+    for (int idx = tid; idx < NTT_TILE; idx += NTT_THREADS) {
+        int r, c;
+        tile_rc(idx, r, c);
         const long gc = gc0 + c;
         u64 v = 0;
         if (gc < a.cols) {
             const long pos = ((gc >> ms) << a.m) + ((long)r << ms) + (gc & (S - 1));
-            v = a.X[pos];
+            if (a.limbs) {
+                const long pr = pos >> a.n, d = pos & (N - 1);
+                if (d < 2L * a.s) {
+                    const u32 limb = a.limbs[pr * a.lda + (d >> 1)];
+                    v = (d & 1) ? (limb >> 16) : (limb & 0xFFFFu);
+                }
+            } else {
+                v = a.X[pos];
+            }
         }
-        sx[r * pitch + c] = v;
+        sx[r * PITCH + c] = v;
     }
     __syncthreads();
-    auto twiddle = [&](bool inv) {
-        if (S == 1) return;                        // sigma = 0: every factor is 1
+    // four-step twiddle of the points (r, c) of a round-2 group
+    auto twiddle = [&](u64 v[G2], int hi, int c) {
+        if (S == 1) return;                      // sigma = 0: every factor is 1
+        const long sigma = (gc0 + c) & (S - 1);
         const unsigned sh = (unsigned)(a.n - a.m);  // w_M = w^(N/M)
-        for (int idx = tid; idx < NTT_TILE; idx += NTT_THREADS) {
-            const int r = idx / C, c = idx - r * C;
-            const long sigma = (gc0 + c) & (S - 1);
-            const unsigned kappa = __brev((unsigned)r) >> (32 - a.k);
+#pragma unroll
+        for (int i = 0; i < G2; ++i) {
+            const unsigned kappa = __brev((unsigned)(G2 * hi + i)) >> (32 - K);
             const unsigned x = (unsigned)((sigma * kappa) << sh);  // < N
-            if (x) {
-                const u64 w = root_pow(a, x);
-                sx[r * pitch + c] = gl_mul(sx[r * pitch + c], w);
-            }
+            if (x) v[i] = gl_mul(v[i], root_pow(a, x));
         }
-        (void)inv;
-        __syncthreads();
     };
-    const int nbf = (R / 2) * C;
+    auto round1 = [&]() {  // stages K-1 .. K2 on groups of G1 points strided by G2
+#pragma unroll
+        for (int q = 0; q < NG1; ++q) {
+            const int gid = tid + NTT_THREADS * q;
+            const int c = gid % C, lo = gid / C;
+            u64 v[G1];
+#pragma unroll
+            for (int i = 0; i < G1; ++i) v[i] = sx[(lo + G2 * i) * PITCH + c];
+            if (!INV) {
+#pragma unroll
+                for (int s = K - 1; s >= K2; --s) {
+                    const int di = 1 << (s - K2);
+#pragma unroll
+                    for (int i0 = 0; i0 < G1; ++i0) {
+                        if (i0 & di) continue;
+                        const int j = lo + G2 * (i0 & (di - 1));
+                        const u64 x = v[i0], y = v[i0 + di];
+                        v[i0] = gl_add(x, y);
+                        v[i0 + di] = gl_mul(gl_sub(x, y), wr[j << (K - 1 - s)]);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int s = K2; s <= K - 1; ++s) {
+                    const int di = 1 << (s - K2);
+#pragma unroll
+                    for (int i0 = 0; i0 < G1; ++i0) {
+                        if (i0 & di) continue;
+                        const int j = lo + G2 * (i0 & (di - 1));
+                        const u64 x = v[i0], y = gl_mul(v[i0 + di], wr[j << (K - 1 - s)]);
+                        v[i0] = gl_add(x, y);
+                        v[i0 + di] = gl_sub(x, y);
+                    }
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < G1; ++i) sx[(lo + G2 * i) * PITCH + c] = v[i];
+        }
+    };
+    auto round2 = [&]() {  // stages K2-1 .. 0 on groups of G2 consecutive points
+#pragma unroll
+        for (int q = 0; q < NG2; ++q) {
+            const int gid = tid + NTT_THREADS * q;
+            const int c = gid % C, hi = gid / C;
+            u64 v[G2];
+#pragma unroll
+            for (int i = 0; i < G2; ++i) v[i] = sx[(G2 * hi + i) * PITCH + c];
+            if (!INV) {
+#pragma unroll
+                for (int s = K2 - 1; s >= 0; --s) {
+                    const int di = 1 << s;
+#pragma unroll
+                    for (int i0 = 0; i0 < G2; ++i0) {
+                        if (i0 & di) continue;
+                        const int j = i0 & (di - 1);
+                        const u64 x = v[i0], y = v[i0 + di];
+                        v[i0] = gl_add(x, y);
+                        v[i0 + di] = gl_mul(gl_sub(x, y), wr[j << (K - 1 - s)]);
+                    }
+                }
+                twiddle(v, hi, c);
+            } else {
+                twiddle(v, hi, c);
+#pragma unroll
+                for (int s = 0; s < K2; ++s) {
+                    const int di = 1 << s;
+#pragma unroll
+                    for (int i0 = 0; i0 < G2; ++i0) {
+                        if (i0 & di) continue;
+                        const int j = i0 & (di - 1);
+                        const u64 x = v[i0], y = gl_mul(v[i0 + di], wr[j << (K - 1 - s)]);
+                        v[i0] = gl_add(x, y);
+                        v[i0 + di] = gl_sub(x, y);
+                    }
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < G2; ++i) sx[(G2 * hi + i) * PITCH + c] = v[i];
+        }
+    };
     if (!INV) {
-        for (int s = a.k - 1; s >= 0; --s) {
-            const int hs = 1 << s;
-            for (int bf = tid; bf < nbf; bf += NTT_THREADS) {
-                const int q = bf / C, c = bf - q * C;
-                const int j = q & (hs - 1);
-                const int r0 = ((q >> s) << (s + 1)) + j, r1 = r0 + hs;
-                const u64 x = sx[r0 * pitch + c], y = sx[r1 * pitch + c];
-                sx[r0 * pitch + c] = gl_add(x, y);
-                sx[r1 * pitch + c] = gl_mul(gl_sub(x, y), wr[j << (a.k - 1 - s)]);
-            }
-            __syncthreads();
-        }
-        twiddle(false);
+        round1();
+        __syncthreads();
+        round2();
     } else {
-        twiddle(true);
-        for (int s = 0; s < a.k; ++s) {
-            const int hs = 1 << s;
-            for (int bf = tid; bf < nbf; bf += NTT_THREADS) {
-                const int q = bf / C, c = bf - q * C;
-                const int j = q & (hs - 1);
-                const int r0 = ((q >> s) << (s + 1)) + j, r1 = r0 + hs;
-                const u64 x = sx[r0 * pitch + c];
-                const u64 y = gl_mul(sx[r1 * pitch + c], wr[j << (a.k - 1 - s)]);
-                sx[r0 * pitch + c] = gl_add(x, y);
-                sx[r1 * pitch + c] = gl_sub(x, y);
-            }
-            __syncthreads();
-        }
+        round2();
+        __syncthreads();
+        round1();
     }
+    __syncthreads();
     for (int idx = tid; idx < NTT_TILE; idx += NTT_THREADS) {
         int r, c;
-        if (S >= C) {
-            r = idx / C;
-            c = idx - r * C;
-        } else {
-            const int blk = idx >> a.m, rem = idx & ((1 << a.m) - 1);
-            r = rem >> ms;
-            c = blk * (int)S + (rem & (int)(S - 1));
-        }
+        tile_rc(idx, r, c);
         const long gc = gc0 + c;
         if (gc < a.cols) {
             const long pos = ((gc >> ms) << a.m) + ((long)r << ms) + (gc & (S - 1));
-            a.X[pos] = sx[r * pitch + c];
+            u64 v = sx[r * PITCH + c];
+            if (a.mulby) v = gl_mul(gl_mul(v, a.mulby[pos]), a.ninv);
+            else if (a.square) v = gl_mul(gl_mul(v, v), a.ninv);
+            a.X[pos] = v;
         }
     }
-}
-
-// Digit vectors: point i of product p is digit i (16 bits) of row p, zero from 2s on.
-__global__ void ntt_digits_kernel(const u32* A, long lda, int s, u64* X, int n, long P) {
-    const long N = 1L << n;
-    const long total = P * N;
-    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total;
-         i += (long)gridDim.x * blockDim.x) {
-        const long p = i >> n;
-        const long d = i & (N - 1);
-        u64 v = 0;
-        if (d < 2L * s) {
-            const u32 limb = A[p * lda + (d >> 1)];
-            v = (d & 1) ? (limb >> 16) : (limb & 0xFFFFu);
-        }
-        X[i] = v;
-    }
-}
-
-// Z = X Y N^-1 pointwise (Y == X: squares).
-__global__ void ntt_pointwise_kernel(u64* X, const u64* Y, long total, u64 ninv) {
-    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total;
-         i += (long)gridDim.x * blockDim.x)
-        X[i] = gl_mul(gl_mul(X[i], Y[i]), ninv);
 }
 
 // Column sum of output limb j (coefficient c_k at bit 16 k, c_k < 2^56).
@@ -405,7 +460,30 @@ size_t ntt_work_bytes(int s, long P, bool square) {
     return (square ? 1 : 2) * pts * 8 + (((size_t)P * nseg + 255) / 256) * 256;
 }
 
-static cudaError_t run_passes(u64* X, long P, int n, const NttTables& t, bool inv, cudaStream_t st) {
+template <bool INV>
+static cudaError_t launch_pass(const NttPassArgs& a, int k, cudaStream_t st) {
+    const int R = 1 << k, C = NTT_TILE / R;
+    const size_t smem = (size_t)R * (C + 1) * 8;
+    const unsigned grid = (unsigned)((a.cols + C - 1) / C);
+    switch (k) {
+#define TC_NTT_PASS(KK)                                                           \
+    case KK:                                                                      \
+        ntt_pass_kernel<INV, KK><<<grid, NTT_THREADS, smem, st>>>(a);             \
+        break;
+        TC_NTT_PASS(1) TC_NTT_PASS(2) TC_NTT_PASS(3) TC_NTT_PASS(4)
+        TC_NTT_PASS(5) TC_NTT_PASS(6) TC_NTT_PASS(7) TC_NTT_PASS(8)
+#undef TC_NTT_PASS
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+// The passes of one forward (top field first) or inverse (bottom field first)
+// transform of P x 2^n points.  `limbs`: the first forward pass reads the
+// digits of these rows; `mulby`: the last forward pass multiplies its outputs
+// by mulby and N^-1 (the pointwise product); `square`: by themselves and N^-1.
+static cudaError_t run_passes(u64* X, long P, int n, const NttTables& t, bool inv, const u32* limbs,
+                              long lda, int s, const u64* mulby, bool square, cudaStream_t st) {
     const std::vector<int> ks = ntt_fields(n);
     std::vector<int> ms(ks.size());
     int m = n;
@@ -413,37 +491,27 @@ static cudaError_t run_passes(u64* X, long P, int n, const NttTables& t, bool in
         ms[j] = m;
         m -= ks[j];
     }
-    static std::once_flag attr;
-    std::call_once(attr, [] {
-        const int smem = (NTT_TILE / 2 + 1) * 8 + (NTT_TILE + (1 << NTT_KMAX)) * 8;
-        cudaFuncSetAttribute(ntt_pass_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        cudaFuncSetAttribute(ntt_pass_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    });
     for (size_t q = 0; q < ks.size(); ++q) {
         const size_t j = inv ? ks.size() - 1 - q : q;
         NttPassArgs a;
         a.X = X;
         a.n = n;
         a.m = ms[j];
-        a.k = ks[j];
         a.cols = (P << n) >> ks[j];
         a.tlo = inv ? t.inv_lo : t.fwd_lo;
         a.thi = inv ? t.inv_hi : t.fwd_hi;
         a.h = t.h;
-        const int R = 1 << a.k, C = NTT_TILE / R;
-        const size_t smem = (size_t)(R / 2 > 0 ? R / 2 : 1) * 8 + (size_t)R * (C + 1) * 8;
-        const unsigned grid = (unsigned)((a.cols + C - 1) / C);
-        if (inv) ntt_pass_kernel<true><<<grid, NTT_THREADS, smem, st>>>(a);
-        else ntt_pass_kernel<false><<<grid, NTT_THREADS, smem, st>>>(a);
-        const cudaError_t e = cudaGetLastError();
+        a.limbs = (!inv && q == 0) ? limbs : nullptr;
+        a.lda = lda;
+        a.s = s;
+        const bool last_fwd = !inv && q + 1 == ks.size();
+        a.mulby = last_fwd ? mulby : nullptr;
+        a.square = last_fwd && square ? 1 : 0;
+        a.ninv = t.ninv;
+        const cudaError_t e = inv ? launch_pass<true>(a, ks[j], st) : launch_pass<false>(a, ks[j], st);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
-}
-
-static unsigned flat_grid(long items, int threads) {
-    const long b = (items + threads - 1) / threads;
-    return (unsigned)std::max<long>(1, std::min<long>(b, 152L * 64));
 }
 
 // P products of s x s limbs (rows of A and Bm), 2s-limb results at OUT + p ldo.
@@ -459,22 +527,18 @@ cudaError_t launch_ntt_mul(const u32* A, long lda, const u32* Bm, long ldb, u32*
     u64* X = static_cast<u64*>(work);
     u64* Y = square ? X : X + total;
     uint8_t* flags = reinterpret_cast<uint8_t*>(X + (square ? 1 : 2) * total);
-    ntt_digits_kernel<<<flat_grid(total, 256), 256, 0, st>>>(A, lda, s, X, n, P);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = run_passes(X, P, n, t, false, st)) != cudaSuccess) return e;
-    if (!square) {
-        ntt_digits_kernel<<<flat_grid(total, 256), 256, 0, st>>>(Bm, ldb, s, Y, n, P);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        if ((e = run_passes(Y, P, n, t, false, st)) != cudaSuccess) return e;
-    }
-    ntt_pointwise_kernel<<<flat_grid(total, 256), 256, 0, st>>>(X, Y, total, t.ninv);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = run_passes(X, P, n, t, true, st)) != cudaSuccess) return e;
+    // X = transform of a's digits; Y = transform of b's digits, multiplied by X and
+    // N^-1 in its last pass (squares: X times itself); then the inverse of Y
+    u64* Z = square ? X : Y;
+    if ((e = run_passes(X, P, n, t, false, A, lda, s, nullptr, square, st)) != cudaSuccess) return e;
+    if (!square && (e = run_passes(Y, P, n, t, false, Bm, ldb, s, X, false, st)) != cudaSuccess)
+        return e;
+    if ((e = run_passes(Z, P, n, t, true, nullptr, 0, s, nullptr, false, st)) != cudaSuccess) return e;
     const int out_len = 2 * s;
     const int nseg = (out_len + CARRY_SEG - 1) / CARRY_SEG;
     const long warps = P * nseg;
     const unsigned grid = (unsigned)((warps * 32 + 255) / 256);
-    ntt_carry_kernel<<<grid, 256, 0, st>>>(X, n, OUT, ldo, out_len, nseg, P, flags);
+    ntt_carry_kernel<<<grid, 256, 0, st>>>(Z, n, OUT, ldo, out_len, nseg, P, flags);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (nseg > 1) {
         ntt_carry_fix_kernel<<<grid, 256, 0, st>>>(OUT, ldo, out_len, nseg, P, flags);
