@@ -93,11 +93,12 @@ tc_status tc_create(tc_ctx **ctx, int device, size_t hbm_budget_bytes,
 /* Free the context and its scratch (synchronises the device first). */
 void tc_destroy(tc_ctx *ctx);
 
-/* Wait for `stream`, then report the context's sticky bounded-wait error word:
- * TC_ETIMEOUT (the word is cleared) if a segment-parallel level of any multiply
- * call on this context since the last check gave up a wait -- those results are
- * invalid -- else TC_OK.  Prepared batches and pipes keep their own words
- * (tc_batch_check, tc_pipe_wait). */
+/* Wait for `stream`, then report the context's sticky device error word (the
+ * word is cleared by the report): TC_EINVAL if a device-side table entry of
+ * tc_mul_batch_dev was out of range, else TC_ETIMEOUT if a segment-parallel
+ * level of any multiply call on this context since the last check gave up a
+ * wait -- those results are invalid -- else TC_OK.  Prepared batches and pipes
+ * keep their own words (tc_batch_check, tc_pipe_wait). */
 tc_status tc_check(tc_ctx *ctx, void *stream);
 
 /* The plan the library would use for balanced operands of `limbs` limbs. */
@@ -109,6 +110,11 @@ tc_status tc_scratch_bytes(tc_ctx *ctx, size_t count, size_t limbs, const tc_opt
                            size_t *bytes_out);
 
 /*
+ * The product w = u v of Section 1 (u = U(2^b), v = V(2^b), w = W(2^b)) by
+ * B-way Toom-Cook with the context's plan: evaluation at the 2B-1 points of
+ * Section 6 by the even-odd parts (Section 4, eq. 4.1-4.2), pointwise products
+ * recursively (Section 2), interpolation by the even-odd combine (eq. 4.5-4.6)
+ * and Newton's divided differences (Theorems 3.2 and 3.3), recomposition.
  * out[0 .. na+nb) = a[0 .. na) * b[0 .. nb)   (device pointers).
  * Exactly na+nb limbs are written (leading zeros kept).  na == 0 or nb == 0
  * zero-fills out.  a == b with na == nb selects the squaring path.
@@ -121,12 +127,15 @@ tc_status tc_scratch_bytes(tc_ctx *ctx, size_t count, size_t limbs, const tc_opt
 tc_status tc_mul(tc_ctx *ctx, const uint32_t *a, size_t na, const uint32_t *b, size_t nb,
                  uint32_t *out, const tc_opts *opts, void *stream);
 
-/* out[0 .. 2 na) = a^2 (device pointers). */
+/* out[0 .. 2 na) = a^2 (device pointers): tc_mul with U = V, one evaluation
+ * per level and squares in the base case (all pointwise products are >= 0). */
 tc_status tc_sqr(tc_ctx *ctx, const uint32_t *a, size_t na, uint32_t *out,
                  const tc_opts *opts, void *stream);
 
 /*
- * `count` independent products in one call.  A, Bv and OUT are device limb
+ * `count` independent products in one call: the paper runs the 2B-1 top-level
+ * products of one multiplication in parallel (Section 2, eq. 2.5); here every
+ * product of a list is batched level by level.  A, Bv and OUT are device limb
  * buffers; a_off/a_len, b_off/b_len and out_off are HOST int64 arrays of
  * limb offsets and lengths.  Product k reads A[a_off[k] .. +a_len[k]) and
  * Bv[b_off[k] .. +b_len[k]) and writes OUT[out_off[k] .. +a_len[k]+b_len[k]).
@@ -140,6 +149,24 @@ tc_status tc_mul_batch(tc_ctx *ctx, size_t count,
                        const uint32_t *Bv, const int64_t *b_off, const int64_t *b_len,
                        uint32_t *OUT, const int64_t *out_off,
                        const tc_opts *opts, void *stream);
+
+/*
+ * The same products with DEVICE int64 tables a_off/a_len, b_off/b_len and
+ * out_off (built on the device, read only by kernels: the call never waits for
+ * the device and can be captured into a CUDA graph once the context has run the
+ * same count and max_limbs).  Without the lengths on the host the products
+ * cannot be grouped into size classes: every product is padded to the one
+ * balanced class that holds `max_limbs` (0 < max_limbs <= 2^28), so uneven
+ * batches do more work than with tc_mul_batch or a prepared batch.  A product
+ * whose offset is negative or whose length is negative or above max_limbs is
+ * skipped on the device (its output is not written) and tc_check then reports
+ * TC_EINVAL.
+ */
+tc_status tc_mul_batch_dev(tc_ctx *ctx, size_t count,
+                           const uint32_t *A, const int64_t *a_off, const int64_t *a_len,
+                           const uint32_t *Bv, const int64_t *b_off, const int64_t *b_len,
+                           uint32_t *OUT, const int64_t *out_off, size_t max_limbs,
+                           const tc_opts *opts, void *stream);
 
 /*
  * Prepared batches (the scheduler's work lists; CUDA-graph replay).  The

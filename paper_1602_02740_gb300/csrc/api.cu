@@ -174,7 +174,7 @@ struct PhaseTimer {
 
 // Run a uniform batch whose scratch is `base` laid out by `L`.
 static __global__ void or_error_kernel(int* sticky, const int* word) {
-    if (threadIdx.x == 0 && *word) *sticky = 1;
+    if (threadIdx.x == 0 && *word) atomicOr(sticky, TC_STICKY_TIMEOUT);
 }
 
 cudaError_t launch_or_error(int* sticky, const int* word, cudaStream_t st) {
@@ -582,6 +582,34 @@ __global__ void scatter_rows(const u32* src, int stride, const int64_t* off, con
         d[i] = s[i];
 }
 
+// Device tables (tc_mul_batch_dev): row k of the padded batch from product k's
+// operand, or zeros and the sticky "invalid" bit when the entry is out of range.
+__global__ void gather_rows_checked(const u32* src, const int64_t* off, const int64_t* len, int s,
+                                    int64_t max_len, u32* dst, int count, int* sticky) {
+    const int k = blockIdx.y;
+    if (k >= count) return;
+    const int64_t L = len[k], o = off[k];
+    const bool ok = L >= 0 && L <= max_len && o >= 0;
+    if (!ok && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(sticky, TC_STICKY_INVALID);
+    const u32* a = src + (ok ? o : 0);
+    u32* d = dst + (long)k * s;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < s; i += gridDim.x * blockDim.x)
+        d[i] = ok && i < L ? a[i] : 0u;
+}
+
+__global__ void scatter_rows_checked(const u32* src, int stride, const int64_t* off, const int64_t* alen,
+                                     const int64_t* blen, int64_t max_len, u32* dst, int count) {
+    const int k = blockIdx.y;
+    if (k >= count) return;
+    const int64_t la = alen[k], lb = blen[k], o = off[k];
+    if (la < 0 || lb < 0 || la > max_len || lb > max_len || o < 0) return;  // reported by the gather
+    const u32* s = src + (long)k * stride;
+    u32* d = dst + o;
+    const int64_t L = la + lb;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < L; i += (long)gridDim.x * blockDim.x)
+        d[i] = s[i];
+}
+
 }  // namespace
 
 size_t tc::size_class(size_t L) {
@@ -735,6 +763,54 @@ extern "C" tc_status tc_mul_batch(tc_ctx* ctx, size_t count, const uint32_t* A, 
     CK(cudaSetDevice(ctx->device));
     return mul_general(ctx, count, A, a_off, a_len, Bv, b_off, b_len, OUT, out_off, opts,
                        (cudaStream_t)stream);
+}
+
+// Products listed by DEVICE (offset, length) tables: the host never reads them.
+// Every product is padded to the balanced size class of max_limbs; entries out of
+// range are skipped on the device and raise the context's "invalid" bit.
+extern "C" tc_status tc_mul_batch_dev(tc_ctx* ctx, size_t count, const uint32_t* A,
+                                      const int64_t* a_off, const int64_t* a_len, const uint32_t* Bv,
+                                      const int64_t* b_off, const int64_t* b_len, uint32_t* OUT,
+                                      const int64_t* out_off, size_t max_limbs, const tc_opts* opts,
+                                      void* stream) {
+    if (!ctx) return TC_EINVAL;
+    if (count == 0) return TC_OK;
+    if (!A || !Bv || !OUT || !a_off || !a_len || !b_off || !b_len || !out_off) return TC_EINVAL;
+    if (max_limbs == 0 || max_limbs > ((size_t)1 << 28) || count > ((size_t)1 << 31)) return TC_EINVAL;
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t s = size_class(max_limbs);
+    tc_opts o;
+    tc_status e = resolve_plan(ctx, s, opts, o);
+    if (e) return e;
+    const BatchLayout L = layout_for(count, s, o, false);
+    const size_t rows_bytes = align256(count * s * 4);
+    e = ensure_arena(ctx, L.total + 2 * rows_bytes + align256(count * 2 * s * 4), st);
+    if (e) return e;
+    char* base = (char*)ctx->arena;
+    u32* rA = (u32*)(base + L.total);
+    u32* rB = (u32*)((char*)rA + rows_bytes);
+    u32* rO = (u32*)((char*)rB + rows_bytes);
+    for (size_t c0 = 0; c0 < count; c0 += 65535) {
+        const int cc = (int)std::min<size_t>(65535, count - c0);
+        dim3 grid((unsigned)std::min<size_t>((s + 255) / 256, 64), cc);
+        gather_rows_checked<<<grid, 256, 0, st>>>(A, a_off + c0, a_len + c0, (int)s, (int64_t)max_limbs,
+                                                  rA + c0 * s, cc, ctx->err_dev);
+        gather_rows_checked<<<grid, 256, 0, st>>>(Bv, b_off + c0, b_len + c0, (int)s, (int64_t)max_limbs,
+                                                  rB + c0 * s, cc, ctx->err_dev);
+    }
+    CK(cudaGetLastError());
+    e = run_uniform(L, base, count, s, rA, (long)s, rB, (long)s, rO, (long)(2 * s), false, st, ctx,
+                    ctx->err_dev);
+    if (e) return e;
+    for (size_t c0 = 0; c0 < count; c0 += 65535) {
+        const int cc = (int)std::min<size_t>(65535, count - c0);
+        dim3 grid((unsigned)std::min<size_t>((2 * s + 255) / 256, 64), cc);
+        scatter_rows_checked<<<grid, 256, 0, st>>>(rO + c0 * 2 * s, (int)(2 * s), out_off + c0,
+                                                   a_len + c0, b_len + c0, (int64_t)max_limbs, OUT, cc);
+    }
+    CK(cudaGetLastError());
+    return TC_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -909,7 +985,7 @@ extern "C" tc_status tc_check(tc_ctx* ctx, void* stream) {
     CK(cudaMemcpy(&flag, ctx->err_dev, sizeof flag, cudaMemcpyDeviceToHost));
     if (flag) {
         CK(cudaMemset(ctx->err_dev, 0, sizeof flag));
-        return TC_ETIMEOUT;
+        return (flag & TC_STICKY_INVALID) ? TC_EINVAL : TC_ETIMEOUT;
     }
     return TC_OK;
 }

@@ -37,7 +37,11 @@ tc_status run_uniform(const BatchLayout& L, char* base, size_t count, size_t s, 
                       long lda, const uint32_t* Bm, long ldb, uint32_t* OUT, long ldo, bool square,
                       cudaStream_t st, tc_ctx* ctx, int* sticky);
 
-// *sticky |= *word on `st` (one thread).
+// Bits of a sticky device error word.
+constexpr int TC_STICKY_TIMEOUT = 1;  // a bounded wait gave up
+constexpr int TC_STICKY_INVALID = 2;  // a device-side table entry was out of range
+
+// *sticky |= TC_STICKY_TIMEOUT if *word is set, on `st` (one thread).
 cudaError_t launch_or_error(int* sticky, const int* word, cudaStream_t st);
 
 // Padded balanced length class of an operand length (at most 50% padding).

@@ -76,6 +76,8 @@ _SIGS = {
     "tc_sqr": (ctypes.c_int, [_vp, _u32p, _sz, _u32p, _optp, _vp]),
     "tc_mul_batch": (ctypes.c_int, [_vp, _sz, _u32p, _i64p, _i64p, _u32p, _i64p, _i64p, _u32p,
                                     _i64p, _optp, _vp]),
+    "tc_mul_batch_dev": (ctypes.c_int, [_vp, _sz, _u32p, _i64p, _i64p, _u32p, _i64p, _i64p, _u32p,
+                                        _i64p, _sz, _optp, _vp]),
     "tc_batch_prepare": (ctypes.c_int, [_vp, _sz, _i64p, _i64p, _i64p, _i64p, _i64p, _optp,
                                         ctypes.POINTER(ctypes.c_void_p)]),
     "tc_batch_run": (ctypes.c_int, [_vp, _vp, _u32p, _u32p, _u32p, _vp]),
@@ -323,6 +325,18 @@ def tc_mul_batch(ctx: Context, A, a_off, a_len, B, b_off, b_len, OUT, out_off, p
     _check(lib().tc_mul_batch(ctx.handle, count, _ptr(A), arrs[0].ctypes.data, arrs[1].ctypes.data,
                               _ptr(B), arrs[2].ctypes.data, arrs[3].ctypes.data, _ptr(OUT),
                               arrs[4].ctypes.data, _opts(plan), _stream(stream)), "tc_mul_batch")
+    return OUT
+
+
+def tc_mul_batch_dev(ctx: Context, A, a_off, a_len, B, b_off, b_len, OUT, out_off, max_limbs: int,
+                     plan=None, stream=None):
+    """Packed batch with DEVICE int64 offset/length tensors (never read by the host)."""
+    for t in (a_off, a_len, b_off, b_len, out_off):
+        if not (t.is_cuda and t.dtype.itemsize == 8):
+            raise ValueError("tables must be int64 device tensors")
+    _check(lib().tc_mul_batch_dev(ctx.handle, a_off.numel(), _ptr(A), _ptr(a_off), _ptr(a_len),
+                                  _ptr(B), _ptr(b_off), _ptr(b_len), _ptr(OUT), _ptr(out_off),
+                                  int(max_limbs), _opts(plan), _stream(stream)), "tc_mul_batch_dev")
     return OUT
 
 

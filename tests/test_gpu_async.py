@@ -130,3 +130,89 @@ def test_mixed_batch_calls_back_to_back(ctx, tc):
             a = A[a_off[k]:a_off[k] + la[k]]
             b = B[b_off[k]:b_off[k] + lb[k]]
             assert np.array_equal(got[o_off[k]:o_off[k] + la[k] + lb[k]], native.schoolbook(a, b))
+
+
+def _packed(count, seed, hi):
+    la, lb = inputs.batch_lengths(count, seed=seed, hi=hi)
+    a_off = np.concatenate([[0], np.cumsum(la)[:-1]]).astype(np.int64)
+    b_off = np.concatenate([[0], np.cumsum(lb)[:-1]]).astype(np.int64)
+    o_off = np.concatenate([[0], np.cumsum(la + lb)[:-1]]).astype(np.int64)
+    A = inputs.uniform(int(la.sum()), seed + 1)
+    B = inputs.uniform(int(lb.sum()), seed + 2)
+    return la, lb, a_off, b_off, o_off, A, B
+
+
+def test_batch_with_device_tables_equals_host_tables(ctx, tc):
+    """tc_mul_batch_dev (device offset/length tables, one padded size class) gives
+    the same products as tc_mul_batch (host tables, size classes), and the
+    oracle's on every product."""
+    import torch
+    t = tc.tc
+    la, lb, a_off, b_off, o_off, A, B = _packed(60, 300, 2500)
+    la[3], lb[3] = 0, 17                         # an empty operand: 17 zero limbs
+    o_off = np.concatenate([[0], np.cumsum(la + lb)[:-1]]).astype(np.int64)
+    dA, dB = t.to_device(A), t.to_device(B)
+    total = int((la + lb).sum())
+    O1 = torch.full((total,), -1, dtype=torch.int32, device="cuda")
+    O2 = torch.full((total,), -1, dtype=torch.int32, device="cuda")
+    t.tc_mul_batch(ctx, dA, a_off, la, dB, b_off, lb, O1, o_off)
+    dev = [torch.from_numpy(x).cuda() for x in (a_off, la, b_off, lb, o_off)]
+    t.tc_mul_batch_dev(ctx, dA, dev[0], dev[1], dB, dev[2], dev[3], O2, dev[4],
+                       max_limbs=int(max(la.max(), lb.max())))
+    t.tc_check(ctx)
+    g1, g2 = t.to_numpy(O1), t.to_numpy(O2)
+    assert np.array_equal(g1, g2)
+    for k in range(len(la)):
+        a = A[a_off[k]:a_off[k] + la[k]]
+        b = B[b_off[k]:b_off[k] + lb[k]]
+        assert np.array_equal(g2[o_off[k]:o_off[k] + la[k] + lb[k]], native.schoolbook(a, b)), k
+
+
+def test_batch_with_device_tables_rejects_bad_entries_on_the_device(ctx, tc):
+    import torch
+    t = tc.tc
+    la, lb, a_off, b_off, o_off, A, B = _packed(8, 400, 900)
+    bad_len = la.copy()
+    bad_len[2] = int(max(la.max(), lb.max())) + 5   # above max_limbs
+    dev = [torch.from_numpy(x).cuda() for x in (a_off, bad_len, b_off, lb, o_off)]
+    O = torch.full((int((la + lb).sum()) + 16,), -1, dtype=torch.int32, device="cuda")
+    t.tc_mul_batch_dev(ctx, t.to_device(A), dev[0], dev[1], t.to_device(B), dev[2], dev[3], O, dev[4],
+                       max_limbs=int(max(la.max(), lb.max())))
+    with pytest.raises(t.TCError) as ei:
+        t.tc_check(ctx)
+    assert ei.value.status == t.TC_EINVAL
+    got = t.to_numpy(O)
+    assert (got[o_off[2]:o_off[2] + la[2] + lb[2]] == 0xFFFFFFFF).all()   # skipped, not written
+    for k in (0, 1, 3):
+        a = A[a_off[k]:a_off[k] + la[k]]
+        b = B[b_off[k]:b_off[k] + lb[k]]
+        assert np.array_equal(got[o_off[k]:o_off[k] + la[k] + lb[k]], native.schoolbook(a, b))
+    t.tc_check(ctx)                               # the report cleared the word
+
+
+def test_batch_with_device_tables_in_a_cuda_graph(ctx, tc):
+    import torch
+    t = tc.tc
+    la, lb, a_off, b_off, o_off, A, B = _packed(40, 500, 4000)
+    dA, dB = t.to_device(A), t.to_device(B)
+    dev = [torch.from_numpy(x).cuda() for x in (a_off, la, b_off, lb, o_off)]
+    O = torch.empty(int((la + lb).sum()), dtype=torch.int32, device="cuda")
+    mx = int(max(la.max(), lb.max()))
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    t.tc_mul_batch_dev(ctx, dA, dev[0], dev[1], dB, dev[2], dev[3], O, dev[4], max_limbs=mx, stream=s)
+    s.synchronize()
+    O.fill_(-1)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        t.tc_mul_batch_dev(ctx, dA, dev[0], dev[1], dB, dev[2], dev[3], O, dev[4], max_limbs=mx,
+                           stream=s)
+    g.replay()
+    torch.cuda.synchronize()
+    t.tc_check(ctx)
+    got = t.to_numpy(O)
+    for k in range(len(la)):
+        a = A[a_off[k]:a_off[k] + la[k]]
+        b = B[b_off[k]:b_off[k] + lb[k]]
+        assert np.array_equal(got[o_off[k]:o_off[k] + la[k] + lb[k]], native.schoolbook(a, b)), k
