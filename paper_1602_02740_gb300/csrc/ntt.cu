@@ -12,10 +12,12 @@
 // zero-padded to N = 2^n >= 4s points; the cyclic convolution of length N of
 // the digit vectors is the exact digit-wise product, because every coefficient
 // is below N (2^16 - 1)^2 < 2^(n + 32) < p for n <= 31.  The transform is a
-// four-step decomposition over fields of the point index (at most 8 bits,
-// 256 points, per pass): each pass runs, for every column of a block, a
+// four-step decomposition over fields of the point index (at most 6 bits,
+// 64 points, per pass): each pass runs, for every column of a block, a
 // radix-2 transform of one field (staged in shared memory, its stages in
-// registers) and multiplies the results by the four-step twiddles.  Forward
+// registers) and multiplies the results by the four-step twiddles.  The
+// transform's root is chosen so that the roots of order <= 64 are powers of 2
+// (see h_root): the sub-transforms multiply by shifts only.  Forward
 // passes go from the top field down and leave the spectrum in a fixed permuted
 // order; the inverse passes undo them in reverse order, so no reordering pass
 // is needed.  The first forward pass reads the digits straight from the limbs
@@ -36,7 +38,7 @@ namespace tc {
 
 constexpr u64 GL_P = 0xFFFFFFFF00000001ull;
 constexpr int NTT_TILE = 4096;       // transform elements per CTA and pass
-constexpr int NTT_KMAX = 8;          // largest field (256-point sub-transforms)
+constexpr int NTT_KMAX = 6;          // largest field (64-point sub-transforms: shifts only)
 constexpr int NTT_THREADS = 256;
 constexpr int CARRY_SEG = 32 * CH;   // output limbs per carry segment (one warp)
 
@@ -52,6 +54,34 @@ __device__ __forceinline__ u64 gl_add(u64 a, u64 b) {
 __device__ __forceinline__ u64 gl_sub(u64 a, u64 b) {
     const u64 d = a - b;
     return a < b ? d + GL_P : d;          // wraps to a - b + p
+}
+
+// (hi 2^64 + lo) mod p, any hi and lo.
+__device__ __forceinline__ u64 gl_reduce(u64 lo, u64 hi) {
+    const u64 hh = hi >> 32, hl = hi & 0xFFFFFFFFull;
+    u64 t = lo - hh;                      // lo - hh 2^96 with 2^96 = -1
+    if (lo < hh) t -= 0xFFFFFFFFull;      // borrow: + p
+    const u64 u = (hl << 32) - hl;        // hl 2^64 with 2^64 = 2^32 - 1
+    u64 r = t + u;
+    if (r < u) r += 0xFFFFFFFFull;        // carry: + 2^64 = + (2^32 - 1)
+    return r >= GL_P ? r - GL_P : r;
+}
+
+// a 2^e mod p for 0 <= e < 96, by shifts: 2^e for e >= 64 is 2^(e-64) 2^64 =
+// 2^(e-32) - 2^(e-64) (mod p).
+__device__ __forceinline__ u64 gl_shl(u64 a, unsigned e) {  // e < 64
+    return e ? gl_reduce(a << e, a >> (64 - e)) : a;
+}
+__device__ __forceinline__ u64 gl_mul_pow2(u64 a, unsigned e) {
+    if (e < 64) return gl_shl(a, e);
+    const u64 x = gl_shl(a, e - 32), y = gl_shl(a, e - 64);
+    return x >= y ? x - y : x - y + GL_P;
+}
+// a 2^-e mod p for 0 <= e < 96: 2^-e = 2^(192 - e) = -2^(96 - e).
+__device__ __forceinline__ u64 gl_mul_pow2_inv(u64 a, unsigned e) {
+    if (!e) return a;
+    const u64 x = gl_mul_pow2(a, 96 - e);
+    return x ? GL_P - x : 0;
 }
 
 __device__ __forceinline__ u64 gl_mul(u64 a, u64 b) {
@@ -81,9 +111,28 @@ static u64 h_pow(u64 a, u64 e) {
     return r;
 }
 
-// A primitive 2^n-th root of unity: g^((p-1) / 2^n) for the generator g = 7
-// of the multiplicative group modulo p.
-static u64 h_root(int n) { return h_pow(7, (GL_P - 1) >> n); }
+// The primitive 2^n-th root of unity the transform uses.  8 = 2^3 has order
+// 64 modulo p (2^96 = -1), so the root is chosen with w^(2^n / 64) = 8: then
+// every root of unity of order <= 64 is a power of 2 and the sub-transforms of
+// at most 64 points multiply by shifts only.  For n >= 6 it is the power of
+// w0 = g^((p-1) / 2^n) (g = 7 generates the multiplicative group) whose
+// (2^n / 64)-th power is 8; for n < 6 it is 8^(64 / 2^n).
+static u64 h_root(int n) {
+    if (n < 6) return h_pow(8, (u64)64 >> n);
+    const u64 w0 = h_pow(7, (GL_P - 1) >> n);
+    const u64 t = h_pow(w0, (u64)1 << (n - 6));  // a primitive 64th root: 8^j for one odd j
+    u64 pw = 8;
+    int j = 1;
+    while (pw != t && j < 64) {
+        pw = h_mul(pw, 64);  // 8^(j + 2)
+        j += 2;
+    }
+    // w0^(j^-1 mod 2^n): its (2^n / 64)-th power is t^(j^-1) = 8
+    u64 inv = 1;  // j^-1 mod 2^n by Newton's iteration (j odd)
+    for (int i = 0; i < 6; ++i) inv *= 2 - (u64)j * inv;
+    inv &= n >= 64 ? ~0ull : (((u64)1 << n) - 1);
+    return h_pow(w0, inv);
+}
 
 // Twiddle tables of one transform length N = 2^n, on one device:
 // w^x = hi[x >> h] lo[x & (2^h - 1)] with w = root(n) (fwd) or its inverse.
@@ -181,14 +230,12 @@ ntt_pass_kernel(NttPassArgs a) {
     constexpr int K1 = (K + 1) / 2, K2 = K / 2;
     constexpr int G1 = 1 << K1, G2 = 1 << K2;
     constexpr int NG1 = NTT_TILE / G1 / NTT_THREADS, NG2 = NTT_TILE / G2 / NTT_THREADS;
-    __shared__ u64 wr[R / 2 > 0 ? R / 2 : 1];   // w_R^t, t < R / 2 (forward or inverse)
+    static_assert(K <= 6, "sub-transform roots are powers of 2 up to 64 points");
     extern __shared__ u64 sx[];                  // [R][PITCH]
     const int ms = a.m - K;                      // log2 S
     const long S = 1L << ms;
     const long gc0 = (long)blockIdx.x * C;
     const int tid = threadIdx.x;
-    const unsigned rstep = 1u << (a.n - K);      // w_R = w^(N/R)
-    for (int t = tid; t < R / 2; t += NTT_THREADS) wr[t] = root_pow(a, (unsigned)t * rstep);
     const long N = 1L << a.n;
     // coalesced tile order: C consecutive columns of one block (S >= C), or C / S
     // whole consecutive blocks (S < C)
@@ -202,9 +249,13 @@ ntt_pass_kernel(NttPassArgs a) {
             c = blk * (int)S + (rem & (int)(S - 1));
         }
     };
-    for (int idx = tid; idx < NTT_TILE; idx += NTT_THREADS) {
+    // every load of the tile in flight before the first store to shared memory
+    constexpr int PER = NTT_TILE / NTT_THREADS;
+    u64 lv[PER];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
         int r, c;
-        tile_rc(idx, r, c);
+        tile_rc(tid + NTT_THREADS * q, r, c);
         const long gc = gc0 + c;
         u64 v = 0;
         if (gc < a.cols) {
@@ -219,7 +270,13 @@ ntt_pass_kernel(NttPassArgs a) {
                 v = a.X[pos];
             }
         }
-        sx[r * PITCH + c] = v;
+        lv[q] = v;
+    }
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        int r, c;
+        tile_rc(tid + NTT_THREADS * q, r, c);
+        sx[r * PITCH + c] = lv[q];
     }
     __syncthreads();
     // four-step twiddle of the points (r, c) of a round-2 group
@@ -252,7 +309,7 @@ ntt_pass_kernel(NttPassArgs a) {
                         const int j = lo + G2 * (i0 & (di - 1));
                         const u64 x = v[i0], y = v[i0 + di];
                         v[i0] = gl_add(x, y);
-                        v[i0 + di] = gl_mul(gl_sub(x, y), wr[j << (K - 1 - s)]);
+                        v[i0 + di] = gl_mul_pow2(gl_sub(x, y), (unsigned)(3 * j) << (5 - s));
                     }
                 }
             } else {
@@ -263,7 +320,7 @@ ntt_pass_kernel(NttPassArgs a) {
                     for (int i0 = 0; i0 < G1; ++i0) {
                         if (i0 & di) continue;
                         const int j = lo + G2 * (i0 & (di - 1));
-                        const u64 x = v[i0], y = gl_mul(v[i0 + di], wr[j << (K - 1 - s)]);
+                        const u64 x = v[i0], y = gl_mul_pow2_inv(v[i0 + di], (unsigned)(3 * j) << (5 - s));
                         v[i0] = gl_add(x, y);
                         v[i0 + di] = gl_sub(x, y);
                     }
@@ -291,7 +348,7 @@ ntt_pass_kernel(NttPassArgs a) {
                         const int j = i0 & (di - 1);
                         const u64 x = v[i0], y = v[i0 + di];
                         v[i0] = gl_add(x, y);
-                        v[i0 + di] = gl_mul(gl_sub(x, y), wr[j << (K - 1 - s)]);
+                        v[i0 + di] = gl_mul_pow2(gl_sub(x, y), (unsigned)(3 * j) << (5 - s));
                     }
                 }
                 twiddle(v, hi, c);
@@ -304,7 +361,7 @@ ntt_pass_kernel(NttPassArgs a) {
                     for (int i0 = 0; i0 < G2; ++i0) {
                         if (i0 & di) continue;
                         const int j = i0 & (di - 1);
-                        const u64 x = v[i0], y = gl_mul(v[i0 + di], wr[j << (K - 1 - s)]);
+                        const u64 x = v[i0], y = gl_mul_pow2_inv(v[i0 + di], (unsigned)(3 * j) << (5 - s));
                         v[i0] = gl_add(x, y);
                         v[i0 + di] = gl_sub(x, y);
                     }
@@ -324,9 +381,10 @@ ntt_pass_kernel(NttPassArgs a) {
         round1();
     }
     __syncthreads();
-    for (int idx = tid; idx < NTT_TILE; idx += NTT_THREADS) {
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
         int r, c;
-        tile_rc(idx, r, c);
+        tile_rc(tid + NTT_THREADS * q, r, c);
         const long gc = gc0 + c;
         if (gc < a.cols) {
             const long pos = ((gc >> ms) << a.m) + ((long)r << ms) + (gc & (S - 1));
@@ -471,7 +529,7 @@ static cudaError_t launch_pass(const NttPassArgs& a, int k, cudaStream_t st) {
         ntt_pass_kernel<INV, KK><<<grid, NTT_THREADS, smem, st>>>(a);             \
         break;
         TC_NTT_PASS(1) TC_NTT_PASS(2) TC_NTT_PASS(3) TC_NTT_PASS(4)
-        TC_NTT_PASS(5) TC_NTT_PASS(6) TC_NTT_PASS(7) TC_NTT_PASS(8)
+        TC_NTT_PASS(5) TC_NTT_PASS(6)
 #undef TC_NTT_PASS
         default: return cudaErrorInvalidValue;
     }

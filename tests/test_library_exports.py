@@ -115,3 +115,15 @@ def test_ntt_roots_of_unity(libtc):
         if n:
             assert pow(w, 1 << (n - 1), p) == p - 1     # primitive: half the order gives -1
     assert libtc.tc_ntt_root(33, ctypes.byref(ctypes.c_uint64())) == -1
+
+
+def test_ntt_root_makes_small_roots_powers_of_two(libtc):
+    """The transform's root w for 2^n points satisfies w^(2^n / 64) = 8 (n >= 6), so
+    every root of unity of order <= 64 it uses is a power of 2 modulo p."""
+    p = (1 << 64) - (1 << 32) + 1
+    libtc.tc_ntt_root.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)]
+    for n in range(6, 33):
+        r = ctypes.c_uint64()
+        assert libtc.tc_ntt_root(n, ctypes.byref(r)) == 0
+        assert pow(r.value, 1 << (n - 6), p) == 8
+    assert pow(8, 64, p) == 1 and pow(8, 32, p) == p - 1     # 8 has order exactly 64
