@@ -319,8 +319,8 @@ tc_status tc_toom_interpolate(size_t count, size_t limbs, int B,
  * one pass as w_i = (sum_p M_ip W(x_p)) / (2^s_i d_i) from the integer form
  * of row i of V^-1 (see tc_interp_matrix_table), with no even-odd combine and
  * no Newton stages.  Same arguments, layout and result as tc_toom_interpolate
- * minus `work` (no scratch).  Supported: B <= 4 and 2e + 2 <= 256 (values of
- * at most 256 limbs, e the evaluation length); otherwise TC_EINVAL.
+ * minus `work` (no scratch).  Supported: B <= 6 and 2e + 2 <= 1024 (values of
+ * at most 1024 limbs, e the evaluation length); otherwise TC_EINVAL.
  */
 tc_status tc_toom_interpolate_matrix(size_t count, size_t limbs, int B,
                                      const uint32_t *Y, size_t ystride,
@@ -328,7 +328,7 @@ tc_status tc_toom_interpolate_matrix(size_t count, size_t limbs, int B,
                                      uint32_t *OUT, size_t ldo, void *stream);
 
 /*
- * Host only (no GPU needed): the integer form of V^-1 for B blocks (2 <= B <= 5)
+ * Host only (no GPU needed): the integer form of V^-1 for B blocks (2 <= B <= 6)
  * on the points 0, +1, -1, +2, -2, ..., +-2^(B-2): for coefficient i and
  * point p, M[i*(2B-1) + p] = M_ip, and V^-1[i][p] = M_ip / (2^shift[i] odd[i])
  * with odd[i] odd, shift[i] and odd[i] the smallest that make row i integral.

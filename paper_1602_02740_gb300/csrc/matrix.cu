@@ -15,8 +15,10 @@
 //
 // Rows of V^-1 come from the Lagrange basis: column p of V^-1 holds the
 // coefficients of prod_(q != p) (X - x_q) divided by prod_(q != p) (x_p - x_q),
-// all in exact integer arithmetic on the host.  For n <= 4 every |M_ip| < 2^25
-// and every d_i < 2^31; the kernel takes n <= 3 and values of at most 256 limbs.
+// all in exact integer arithmetic on the host.  For n <= 5 every |M_ip| < 2^29,
+// sum_p |M_ip| < 2^31 (so the 64-bit column sums of the 2n+1 terms cannot
+// overflow), every d_i < 2^20 and every s_i <= 21; the kernel takes n <= 5 and
+// values of at most 1024 limbs.
 #include <cstring>
 #include <mutex>
 
@@ -29,7 +31,7 @@ namespace tc {
 
 DivConst make_div_const(u32 d, int KL);
 
-constexpr int MAT_MAXN = 4;
+constexpr int MAT_MAXN = 5;
 constexpr int MAT_MAXP = 2 * MAT_MAXN + 1;
 
 struct MatTable {
@@ -122,12 +124,18 @@ const MatTable* mat_table(int n) {
 
 }  // namespace
 
-// One warp per product.  Shared memory per warp: the 2N+1 input rows (YM
-// words each, zero past the 2e valid limbs), then 2N+1 slots of YM + 4 words
-// for the coefficients, each stored shifted by (i b) mod 4 words so that the
-// recomposition reads limb l - i b of it with one aligned 16-byte load.
+// One warp per product, streaming the values in 128-limb chunks.  Shared
+// memory per warp: the current chunk of each of the 2N+1 point values, then
+// 2N+1 slots of YM + 4 words for the coefficients, each stored shifted by
+// (i b) mod 4 words so that the recomposition reads limb l - i b of it with
+// one aligned 16-byte load.  For every chunk and every coefficient i the warp
+// forms the positive and negative column sums of M_ip W(x_p), normalises both,
+// subtracts, and divides exactly by d_i; the normalisation, subtraction and
+// division states of every coefficient are carried from chunk to chunk in
+// registers.  The right shifts by s_i (they read the limb above) run on the
+// slots once all chunks are done.
 template <int N, int NC>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(128)
 interp_matrix_kernel(const u32* __restrict__ y, long ystride, int len, const uint8_t* __restrict__ su,
                      const uint8_t* __restrict__ sv, u32* __restrict__ out, long out_stride,
                      int out_len, int b, MatTable mt, long P) {
@@ -136,49 +144,57 @@ interp_matrix_kernel(const u32* __restrict__ y, long ystride, int len, const uin
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long k = (long)blockIdx.x * (blockDim.x >> 5) + warp;
     if (k >= P) return;  // warp-uniform
-    u32* rows = msm + (long)warp * NP * (YM + SLOT);
-    u32* slots = rows + NP * YM;
+    u32* stage = msm + (long)warp * NP * (C + SLOT);
+    u32* slots = stage + NP * C;
     const u32* yk = y + k * NP * ystride;
-    // ---- the point values, all copies in flight together ----
+    u32 negm = 0;  // bit p: W(x_p) < 0
 #pragma unroll
-    for (int r = 0; r < NP; ++r) {
-        const u32* row = yk + r * ystride;
+    for (int p = 0; p < NP; ++p) {
+        bool sg = false;
+        if (su) sg ^= su[k * NP + p] != 0;
+        if (sv) sg ^= sv[k * NP + p] != 0;
+        negm |= sg ? 1u << p : 0u;
+    }
 #pragma unroll
-        for (int c = 0; c < NC; ++c) {
+    for (int i = 0; i < NP; ++i) {
+        u32* slot = slots + i * SLOT;
+        if (lane < 4) slot[lane] = 0u;
+        if (lane >= 28) slot[YM + lane - 28] = 0u;
+    }
+    UnsignedNorm npos[NP], nneg[NP];
+    u32 bw[NP], dB[NP];
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+        npos[i] = UnsignedNorm{0, 0};
+        nneg[i] = UnsignedNorm{0, 0};
+        bw[i] = 0;
+        dB[i] = 0;
+    }
+    for (int c = 0; c < NC; ++c) {
+        // this chunk of every point value, all copies in flight together
+        __syncwarp();
+#pragma unroll
+        for (int r = 0; r < NP; ++r) {
+            const u32* row = yk + r * ystride;
             const int pos = c * C + 4 * lane;
             const int left = len - pos;
             const unsigned bytes = left >= 4 ? 16u : left > 0 ? 4u * left : 0u;
             asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;"
-                         :: "r"((unsigned)__cvta_generic_to_shared(rows + r * YM + pos)),
+                         :: "r"((unsigned)__cvta_generic_to_shared(stage + r * C + 4 * lane)),
                             "l"(bytes ? row + pos : row), "r"(bytes) : "memory");
         }
-    }
-    cp_async_wait_all();
-    __syncwarp();
-    u32 negm = 0;  // bit p: W(x_p) < 0
+        cp_async_wait_all();
+        __syncwarp();
+        // D_i w_i = sum_p M_ip W(x_p), chunk c, then exact division by d_i
 #pragma unroll
-    for (int p = 0; p < NP; ++p) {
-        bool s = false;
-        if (su) s ^= su[k * NP + p] != 0;
-        if (sv) s ^= sv[k * NP + p] != 0;
-        negm |= s ? 1u << p : 0u;
-    }
-    // ---- w_i = (sum_p M_ip W(x_p)) / (2^s_i d_i) ----
-#pragma unroll
-    for (int i = 0; i < NP; ++i) {
-        UnsignedNorm npos{0, 0}, nneg{0, 0};
-        u32 bw = 0;
-        u32 r[NC][4];
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-            // column sums of the positive and the negative terms (each < 2^48)
+        for (int i = 0; i < NP; ++i) {
             u64 pos[4] = {0, 0, 0, 0}, neg[4] = {0, 0, 0, 0};
 #pragma unroll
             for (int p = 0; p < NP; ++p) {
                 const int m = mt.M[i][p];
                 if (m == 0) continue;
                 const u32 am = (u32)(m < 0 ? -m : m);
-                const uint4 v = ld4(rows + p * YM + c * C + 4 * lane);
+                const uint4 v = ld4(stage + p * C + 4 * lane);
                 if ((m < 0) != (((negm >> p) & 1u) != 0)) {
                     neg[0] += (u64)v.x * am; neg[1] += (u64)v.y * am;
                     neg[2] += (u64)v.z * am; neg[3] += (u64)v.w * am;
@@ -187,39 +203,32 @@ interp_matrix_kernel(const u32* __restrict__ y, long ystride, int len, const uin
                     pos[2] += (u64)v.z * am; pos[3] += (u64)v.w * am;
                 }
             }
-            u32 dp[4], dn[4];
-            warp_norm_unsigned(pos, npos, dp);
-            warp_norm_unsigned(neg, nneg, dn);
-            warp_sub_seg<4>(dp, dn, bw, r[c]);  // D_i w_i >= 0
+            u32 dp[4], dn[4], r[4];
+            warp_norm_unsigned(pos, npos[i], dp);
+            warp_norm_unsigned(neg, nneg[i], dn);
+            warp_sub_seg<4>(dp, dn, bw[i], r);  // D_i w_i >= 0
+            if (mt.odd[i] > 1) warp_exact_div_seg<4>(r, mt.div[i], dB[i]);
+            u32* slot = slots + i * SLOT + ((i * b) & 3) + c * C + 4 * lane;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) slot[j] = r[j];
         }
-        if (mt.odd[i] > 1) {
-            u32 B = 0;
+    }
+    __syncwarp();
+    // w_i = (D_i w_i / d_i) >> s_i, in place, chunks low to high
 #pragma unroll
-            for (int c = 0; c < NC; ++c) warp_exact_div_seg<4>(r[c], mt.div[i], B);
+    for (int i = 0; i < NP; ++i) {
+        const u32 sh = (u32)mt.shift[i];
+        if (!sh) continue;
+        u32* w = slots + i * SLOT + ((i * b) & 3);
+        for (int c = 0; c < NC; ++c) {
+            u32 v[5];
+#pragma unroll
+            for (int j = 0; j < 5; ++j) v[j] = w[c * C + 4 * lane + j];  // the limb above included
+            __syncwarp();
+#pragma unroll
+            for (int j = 0; j < 4; ++j) w[c * C + 4 * lane + j] = fshr(v[j], v[j + 1], sh);
+            __syncwarp();
         }
-        const u32 s = (u32)mt.shift[i];
-        if (s) {
-#pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                const u32 up = __shfl_down_sync(FULL, r[c][0], 1);
-                const u32 nxt = c + 1 < NC ? __shfl_sync(FULL, r[c + 1 < NC ? c + 1 : c][0], 0) : 0u;
-                const u32 above = lane == 31 ? nxt : up;
-                u32 t[4];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) t[j] = fshr(r[c][j], j < 3 ? r[c][j + 1] : above, s);
-#pragma unroll
-                for (int j = 0; j < 4; ++j) r[c][j] = t[j];
-            }
-        }
-        u32* slot = slots + i * SLOT;
-        const int dt = (i * b) & 3;
-        if (lane == 0) { slot[0] = slot[1] = slot[2] = slot[3] = 0u; }
-        if (lane == 31) { slot[YM] = slot[YM + 1] = slot[YM + 2] = slot[YM + 3] = 0u; }
-        __syncwarp();
-#pragma unroll
-        for (int c = 0; c < NC; ++c)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) slot[dt + c * C + 4 * lane + j] = r[c][j];
     }
     __syncwarp();
     // ---- recompose out[l] = sum_i w_i[l - i b] ----
@@ -261,7 +270,7 @@ cudaError_t launch_matrix(const LevelGeom& g, const u32* y, const uint8_t* su, c
     const MatTable* mt = mat_table(N);
     if (!mt) return cudaErrorInvalidValue;
     constexpr int NP = 2 * N + 1, YM = NC * 128;
-    const size_t per_warp = (size_t)NP * (2 * YM + 4) * 4;
+    const size_t per_warp = (size_t)NP * (128 + YM + 4) * 4;
     static int regs_per_warp = 0;
     static std::once_flag once;
     std::call_once(once, [] {
@@ -272,7 +281,7 @@ cudaError_t launch_matrix(const LevelGeom& g, const u32* y, const uint8_t* su, c
                             ? (fa.numRegs + 7) / 8 * 8 * 32 : 128 * 32;
     });
     int wpb = 1, best = 0;
-    for (int w = 1; w <= 8; ++w) {
+    for (int w = 1; w <= 4; ++w) {
         if (w * per_warp > 200 * 1024) break;
         int blocks = (int)((228 * 1024) / (w * per_warp + 1024));
         const int reg_blocks = 65536 / (w * regs_per_warp);
@@ -289,11 +298,15 @@ cudaError_t launch_matrix(const LevelGeom& g, const u32* y, const uint8_t* su, c
 
 }  // namespace
 
-// Values of 2e + 2 limbs (with room for the denominators' growth) in 128-limb chunks.
-static int matrix_chunks(const LevelGeom& g) { return (2 * g.e + 2 + 127) / 128; }
+// Values of 2e + 2 limbs (with room for the denominators' growth) in 128-limb
+// chunks, rounded up to 1, 2, 4 or 8 chunks.
+static int matrix_chunks(const LevelGeom& g) {
+    const int c = (2 * g.e + 2 + 127) / 128;
+    return c <= 1 ? 1 : c <= 2 ? 2 : c <= 4 ? 4 : c <= 8 ? 8 : 0;
+}
 
 bool matrix_interp_supported(const LevelGeom& g) {
-    return g.n >= 1 && g.n <= 3 && matrix_chunks(g) <= 2;
+    return g.n >= 1 && g.n <= MAT_MAXN && matrix_chunks(g) >= 1;
 }
 
 cudaError_t launch_interp_matrix(const LevelGeom& g, const u32* y, const uint8_t* su,
@@ -302,13 +315,16 @@ cudaError_t launch_interp_matrix(const LevelGeom& g, const u32* y, const uint8_t
     if (P <= 0) return cudaSuccess;
     if (!matrix_interp_supported(g)) return cudaErrorInvalidValue;
     const int nc = matrix_chunks(g);
-    switch (g.n * 2 + nc - 1) {
-        case 2: return launch_matrix<1, 1>(g, y, su, sv, out, ldo, out_len, P, st);
-        case 3: return launch_matrix<1, 2>(g, y, su, sv, out, ldo, out_len, P, st);
-        case 4: return launch_matrix<2, 1>(g, y, su, sv, out, ldo, out_len, P, st);
-        case 5: return launch_matrix<2, 2>(g, y, su, sv, out, ldo, out_len, P, st);
-        case 6: return launch_matrix<3, 1>(g, y, su, sv, out, ldo, out_len, P, st);
-        default: return launch_matrix<3, 2>(g, y, su, sv, out, ldo, out_len, P, st);
+    const int ci = nc == 1 ? 0 : nc == 2 ? 1 : nc == 4 ? 2 : 3;
+    switch (g.n * 4 + ci) {
+#define TC_MATRIX_CASE(NN, CI, NCC) \
+    case NN * 4 + CI: return launch_matrix<NN, NCC>(g, y, su, sv, out, ldo, out_len, P, st);
+#define TC_MATRIX_N(NN) TC_MATRIX_CASE(NN, 0, 1) TC_MATRIX_CASE(NN, 1, 2) TC_MATRIX_CASE(NN, 2, 4) \
+    TC_MATRIX_CASE(NN, 3, 8)
+        TC_MATRIX_N(1) TC_MATRIX_N(2) TC_MATRIX_N(3) TC_MATRIX_N(4) TC_MATRIX_N(5)
+#undef TC_MATRIX_N
+#undef TC_MATRIX_CASE
+        default: return cudaErrorInvalidValue;
     }
 }
 

@@ -143,7 +143,9 @@ def test_interpolate_vs_oracle(tc, B, L, kind):
 
 
 MATRIX_CASES = [(2, 4), (2, 100), (2, 250), (3, 9), (3, 150), (3, 300), (3, 378),
-                (4, 16), (4, 200), (4, 457), (4, 504)]
+                (4, 16), (4, 200), (4, 457), (4, 504),
+                # degree 4 and 5, values of up to 8 chunks (the bench's level-1 shape: B = 6, 2735)
+                (5, 30), (5, 600), (5, 2400), (6, 12), (6, 700), (6, 2735), (4, 1900), (2, 1000)]
 
 
 @pytest.mark.parametrize("B,L", MATRIX_CASES)
@@ -203,13 +205,13 @@ def test_interpolate_matrix_many_products(tc):
 def test_interpolate_matrix_rejects_unsupported(tc):
     import torch
     t = tc.tc
-    Y = torch.zeros((1, 9, 64), dtype=torch.int32, device="cuda")
+    Y = torch.zeros((1, 13, 64), dtype=torch.int32, device="cuda")
     with pytest.raises(t.TCError):
-        t.tc_toom_interpolate_matrix(Y, 100, 5)          # B = 5: not supported
-    _, e, _, ystride = t.level_sizes(2000, 4)
+        t.tc_toom_interpolate_matrix(Y, 100, 7)          # B = 7: not supported
+    _, e, _, ystride = t.level_sizes(5000, 4)
     Y = torch.zeros((1, 7, ystride), dtype=torch.int32, device="cuda")
     with pytest.raises(t.TCError):
-        t.tc_toom_interpolate_matrix(Y, 2000, 4)         # values longer than 256 limbs
+        t.tc_toom_interpolate_matrix(Y, 5000, 4)         # values longer than 1024 limbs
 
 
 # ---------------------------------------------------------------- whole product

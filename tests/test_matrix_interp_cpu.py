@@ -22,7 +22,7 @@ def tcmod():
     return tc
 
 
-@pytest.mark.parametrize("B", [2, 3, 4, 5])
+@pytest.mark.parametrize("B", [2, 3, 4, 5, 6])
 def test_table_equals_oracle_inverse(tcmod, B):
     M, shift, odd = tcmod.tc_interp_matrix_table(B)
     Vi = vandermonde.inverse(tuple(vandermonde.points(B)))
@@ -43,10 +43,10 @@ def test_table_rejects_bad_arguments(tcmod):
     with pytest.raises(tcmod.TCError):
         tcmod.tc_interp_matrix_table(1)
     with pytest.raises(tcmod.TCError):
-        tcmod.tc_interp_matrix_table(6)
+        tcmod.tc_interp_matrix_table(7)
 
 
-@pytest.mark.parametrize("B,L", [(2, 10), (3, 40), (4, 457), (5, 100)])
+@pytest.mark.parametrize("B,L", [(2, 10), (3, 40), (4, 457), (5, 100), (6, 300)])
 def test_table_applied_to_point_values(tcmod, B, L):
     """w_i = (sum_p M_ip W(x_p)) / (2^s_i d_i) is exact and equals the oracle's
     coefficients; recomposed it is the product."""
