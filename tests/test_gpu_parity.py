@@ -569,3 +569,50 @@ def test_plain_schoolbook_plan_batch(ctx, tc):
     OUT = host(tc.tc.tc_mul_uniform(ctx, dev(A), dev(B), plan=[]))
     for k in range(count):
         assert same_limbs(OUT[k], native.schoolbook(A[k], B[k]))
+
+
+# ---------------------------------------------------------------- one stage exposed
+# The streaming interpolation kernels leave Theorem 3.3's output in their work
+# buffer: rows (0, m) hold the even polynomial's monomial coefficients ce_m
+# (m = 0..n) and rows (1, m) the odd one's co_m (m = 1..n), each Y limbs, before
+# re-interleaving and recomposition.  (12, 6000) and (9, 3000) run the two-warp
+# kernel, (6, 3000) and (10, 3000) the one-warp kernel.
+
+@pytest.mark.parametrize("B,L", [(12, 6000), (9, 3000), (6, 3000), (10, 3000)])
+def test_interpolation_stage_outputs_vs_oracle(tc, B, L):
+    import torch
+    t = tc.tc
+    count = 2100
+    n = B - 1
+    _, e, _, ystride = t.level_sizes(L, B)
+    K = 8 if 2 * e + 2 > 1536 else 4
+    Yl = -(-(2 * e + 2) // (32 * K)) * (32 * K)
+    g = inputs.rng(31 * B + L)
+    A = g.integers(0, 1 << 32, size=(count, L), dtype=np.uint64).astype(np.uint32)
+    Bm = g.integers(0, 1 << 32, size=(count, L), dtype=np.uint64).astype(np.uint32)
+    A[4] = 0xFFFFFFFF
+    Bm[4] = 0xFFFFFFFF
+    Y = np.zeros((count, 2 * B - 1, ystride), dtype=np.uint32)
+    S = np.zeros((count, 2 * B - 1), dtype=np.uint8)
+    ys = {}
+    for k in range(count):
+        y = _oracle_level(to_int(A[k]), to_int(Bm[k]), L, B)
+        ys[k] = y
+        for p, val in enumerate(y):
+            Y[k, p, :2 * e] = from_int(abs(val), 2 * e)
+            S[k, p] = 1 if val < 0 else 0
+    wb = t.tc_toom_interpolate_work_bytes(count, L, B)
+    assert wb == count * 2 * (n + 1) * Yl * 4, "not a streaming shape"
+    work = torch.zeros(wb, dtype=torch.uint8, device="cuda")
+    out = host(t.tc_toom_interpolate(dev(Y), L, B, SGN_U=torch.from_numpy(S).cuda(), work=work))
+    W = work.cpu().numpy().view(np.uint32).reshape(count, 2, n + 1, Yl)
+    X = toom.nodes(B)
+    for k in (0, 4, 1001, count - 1):
+        ye, yo = toom.even_odd_combine(ys[k])
+        ce = toom.newton_to_monomial(X, toom.divided_differences(X, ye))
+        co = toom.newton_to_monomial(X, toom.divided_differences(X, yo))
+        for m in range(n + 1):
+            assert to_int(W[k, 0, m]) == ce[m], (B, L, k, "ce", m)
+        for m in range(1, n + 1):
+            assert to_int(W[k, 1, m]) == co[m], (B, L, k, "co", m)
+        assert same_limbs(out[k], to_int(A[k]) * to_int(Bm[k])), k
