@@ -140,7 +140,9 @@ tc_status tc_sqr(tc_ctx *ctx, const uint32_t *a, size_t na, uint32_t *out,
  * limb offsets and lengths.  Product k reads A[a_off[k] .. +a_len[k]) and
  * Bv[b_off[k] .. +b_len[k]) and writes OUT[out_off[k] .. +a_len[k]+b_len[k]).
  * Products are grouped into size classes; each class runs level by level
- * (breadth first) with every product of the class in the same launches.
+ * (breadth first) with every product of the class in the same launches, and
+ * the classes run concurrently on streams of the context (each in its own
+ * region of the context's scratch; the call's stream waits for all of them).
  * TC_EINVAL (before any launch) if an offset is negative or above 2^40, or a
  * length is negative or above 2^28 limbs.
  */
@@ -175,8 +177,10 @@ tc_status tc_mul_batch_dev(tc_ctx *ctx, size_t count,
  * level.  tc_batch_prepare does the host side of tc_mul_batch once for a
  * fixed list: it groups the products into size classes (padded balanced
  * lengths), picks each class's plan (`opts` as in tc_mul_batch), uploads the
- * index tables and allocates the scratch of the largest class -- device memory
- * owned by the batch, at most the context's budget (else TC_ENOMEM).  Offsets
+ * index tables and allocates one scratch region per class -- device memory
+ * owned by the batch, at most the context's budget (else TC_ENOMEM) -- and the
+ * streams its classes run on concurrently (a captured run becomes parallel
+ * branches of the graph).  Offsets
  * and lengths are host int64 arrays read during the call only.
  * tc_batch_run then enqueues kernels and memsets on `stream` and nothing else
  * (no allocation, no host memory, no synchronisation), so it may be captured

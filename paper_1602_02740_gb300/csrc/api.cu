@@ -172,6 +172,51 @@ struct PhaseTimer {
     }
 };
 
+cudaError_t StreamFan::init() {
+    if (ready) return cudaSuccess;
+    cudaError_t e = cudaEventCreateWithFlags(&fork_ev, cudaEventDisableTiming);
+    for (int i = 0; i < K && e == cudaSuccess; ++i) {
+        e = cudaStreamCreateWithFlags(&s[i], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join_ev[i], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) {
+        destroy();
+        return e;
+    }
+    ready = true;
+    return cudaSuccess;
+}
+
+void StreamFan::destroy() {
+    for (int i = 0; i < K; ++i) {
+        if (s[i]) {
+            cudaStreamSynchronize(s[i]);
+            cudaStreamDestroy(s[i]);
+        }
+        if (join_ev[i]) cudaEventDestroy(join_ev[i]);
+        s[i] = nullptr;
+        join_ev[i] = nullptr;
+    }
+    if (fork_ev) cudaEventDestroy(fork_ev);
+    fork_ev = nullptr;
+    ready = false;
+}
+
+cudaError_t StreamFan::fork(cudaStream_t st) {
+    cudaError_t e = cudaEventRecord(fork_ev, st);
+    for (int i = 0; i < K && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(s[i], fork_ev, 0);
+    return e;
+}
+
+cudaError_t StreamFan::join(cudaStream_t st) {
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < K && e == cudaSuccess; ++i) {
+        e = cudaEventRecord(join_ev[i], s[i]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, join_ev[i], 0);
+    }
+    return e;
+}
+
 // Run a uniform batch whose scratch is `base` laid out by `L`.
 static __global__ void or_error_kernel(int* sticky, const int* word) {
     if (threadIdx.x == 0 && *word) atomicOr(sticky, TC_STICKY_TIMEOUT);
@@ -342,6 +387,7 @@ extern "C" void tc_destroy(tc_ctx* ctx) {
     if (ctx->arena) cudaFree(ctx->arena);
     if (ctx->aux) cudaFree(ctx->aux);
     if (ctx->err_dev) cudaFree(ctx->err_dev);
+    ctx->fan.destroy();
     for (int i = 0; i < 2; ++i) {
         if (ctx->pin[i]) cudaFreeHost(ctx->pin[i]);
         if (ctx->pin_ev[i]) cudaEventDestroy(ctx->pin_ev[i]);
@@ -660,8 +706,9 @@ static tc_status stage_tables(tc_ctx* ctx, size_t bytes, void** host) {
 
 // Products listed by (offset, length) triples; all device limb buffers, host index arrays
 // (validated by batch_tables_valid).  Asynchronous: the tables of every size class
-// go to the device in one copy from pinned staging, and the classes run one after
-// another on the stream sharing one scratch region.
+// go to the device in one copy from pinned staging; the classes are independent, so
+// each gets its own scratch region and they run concurrently on the context's stream
+// fan (a class of a few hundred products alone leaves most of the GPU idle).
 static tc_status mul_general(tc_ctx* ctx, size_t count, const u32* A, const int64_t* a_off,
                              const int64_t* a_len, const u32* Bm, const int64_t* b_off,
                              const int64_t* b_len, u32* OUT, const int64_t* out_off,
@@ -681,9 +728,9 @@ static tc_status mul_general(tc_ctx* ctx, size_t count, const u32* A, const int6
     }
     if (items.empty()) return TC_OK;
     std::sort(items.begin(), items.end(), [](const Item& x, const Item& y) { return x.cls < y.cls; });
-    struct Class { size_t s, cnt, first; BatchLayout L; };
+    struct Class { size_t s, cnt, first, off; BatchLayout L; };
     std::vector<Class> classes;
-    size_t need = 0;
+    size_t need = 0;  // sum of the classes' regions
     for (size_t i = 0; i < items.size();) {
         size_t j = i;
         while (j < items.size() && items[j].cls == items[i].cls) ++j;
@@ -694,7 +741,8 @@ static tc_status mul_general(tc_ctx* ctx, size_t count, const u32* A, const int6
         // a caller's plan applies to every size class it is valid for
         const tc_opts o = (opts && plan_valid(*opts, c.s)) ? *opts : plan_for(ctx, c.s);
         c.L = layout_for(c.cnt, c.s, o, false);
-        need = std::max(need, c.L.total + 2 * align256(c.cnt * c.s * 4) + align256(c.cnt * 2 * c.s * 4));
+        c.off = need;
+        need += align256(c.L.total + 2 * align256(c.cnt * c.s * 4) + align256(c.cnt * 2 * c.s * 4));
         classes.push_back(std::move(c));
         i = j;
     }
@@ -715,12 +763,21 @@ static tc_status mul_general(tc_ctx* ctx, size_t count, const u32* A, const int6
         h[4 * N + t] = out_off[k];
         h[5 * N + t] = a_len[k] + b_len[k];
     }
-    char* base = (char*)ctx->arena;
-    int64_t* dtab = (int64_t*)(base + align256(need));
+    char* arena = (char*)ctx->arena;
+    int64_t* dtab = (int64_t*)(arena + align256(need));
     CK(cudaMemcpyAsync(dtab, h, tab_bytes, cudaMemcpyHostToDevice, st));
     CK(cudaEventRecord(ctx->pin_ev[ctx->pin_turn], st));
     ctx->pin_turn ^= 1;
-    for (const Class& c : classes) {
+    const bool fan = classes.size() > 1;
+    if (fan) {
+        CK(ctx->fan.init());
+        CK(ctx->fan.fork(st));
+    }
+    // the largest classes first, each on the next stream of the fan
+    for (size_t ci = classes.size(); ci-- > 0;) {
+        const Class& c = classes[ci];
+        const cudaStream_t cs = fan ? ctx->fan.s[(classes.size() - 1 - ci) % StreamFan::K] : st;
+        char* base = arena + c.off;
         const size_t s = c.s, cnt = c.cnt;
         u32* rA = (u32*)(base + c.L.total);
         u32* rB = (u32*)((char*)rA + align256(cnt * s * 4));
@@ -734,21 +791,22 @@ static tc_status mul_general(tc_ctx* ctx, size_t count, const u32* A, const int6
         for (size_t c0 = 0; c0 < cnt; c0 += 65535) {
             const int cc = (int)std::min<size_t>(65535, cnt - c0);
             dim3 grid((unsigned)std::min<size_t>((s + 255) / 256, 64), cc);
-            gather_rows<<<grid, 256, 0, st>>>(A, aoff + c0, alen + c0, (int)s, rA + c0 * s, cc);
-            gather_rows<<<grid, 256, 0, st>>>(Bm, boff + c0, blen + c0, (int)s, rB + c0 * s, cc);
+            gather_rows<<<grid, 256, 0, cs>>>(A, aoff + c0, alen + c0, (int)s, rA + c0 * s, cc);
+            gather_rows<<<grid, 256, 0, cs>>>(Bm, boff + c0, blen + c0, (int)s, rB + c0 * s, cc);
         }
         CK(cudaGetLastError());
-        e = run_uniform(c.L, base, cnt, s, rA, (long)s, rB, (long)s, rO, (long)(2 * s), false, st, ctx,
+        e = run_uniform(c.L, base, cnt, s, rA, (long)s, rB, (long)s, rO, (long)(2 * s), false, cs, ctx,
                         ctx->err_dev);
         if (e) return e;
         for (size_t c0 = 0; c0 < cnt; c0 += 65535) {
             const int cc = (int)std::min<size_t>(65535, cnt - c0);
             dim3 grid((unsigned)std::min<size_t>((2 * s + 255) / 256, 64), cc);
-            scatter_rows<<<grid, 256, 0, st>>>(rO + c0 * 2 * s, (int)(2 * s), ooff + c0, olen + c0,
+            scatter_rows<<<grid, 256, 0, cs>>>(rO + c0 * 2 * s, (int)(2 * s), ooff + c0, olen + c0,
                                                OUT, cc);
         }
         CK(cudaGetLastError());
     }
+    if (fan) CK(ctx->fan.join(st));
     return TC_OK;
 }
 
@@ -825,14 +883,16 @@ struct tc_batch {
         size_t s = 0, cnt = 0;
         BatchLayout L;
         size_t tab = 0;  // first entry of this class in each index table
+        size_t off = 0;  // this class's region of the scratch
     };
     std::vector<Class> classes;
     std::vector<std::pair<int64_t, int64_t>> zeros;  // (out offset, limbs) of empty products
     int64_t* tables = nullptr;  // device: aoff, alen, boff, blen, ooff, olen (each `total` long)
     size_t total = 0;
-    char* scratch = nullptr;    // device: max over classes of level scratch + rows + outputs
+    char* scratch = nullptr;    // device: one region per class (level scratch + rows + outputs)
     size_t scratch_bytes = 0;
     int* err_dev = nullptr;     // device: sticky bounded-wait error word of the runs
+    StreamFan fan;              // the classes run concurrently on these
 };
 
 extern "C" void tc_batch_destroy(tc_batch* bt);
@@ -873,7 +933,8 @@ extern "C" tc_status tc_batch_prepare(tc_ctx* ctx, size_t count, const int64_t* 
         c.tab = i;
         const tc_opts o = (opts && plan_valid(*opts, c.s)) ? *opts : plan_for(ctx, c.s);
         c.L = layout_for(c.cnt, c.s, o, false);
-        need = std::max(need, c.L.total + class_extra(c.cnt, c.s));
+        c.off = need;
+        need += align256(c.L.total + class_extra(c.cnt, c.s));
         for (size_t t = i; t < j; ++t) {
             const size_t k = items[t].k;
             h[t] = a_off[k];
@@ -896,6 +957,7 @@ extern "C" tc_status tc_batch_prepare(tc_ctx* ctx, size_t count, const int64_t* 
     if (cudaMalloc(&bt->err_dev, 256) != cudaSuccess) { cudaGetLastError(); return fail(TC_ENOMEM); }
     cudaError_t e = cudaMemset(bt->err_dev, 0, 256);
     if (e != cudaSuccess) return fail(tc_fail_cuda(e));
+    if (bt->classes.size() > 1 && (e = bt->fan.init()) != cudaSuccess) return fail(tc_fail_cuda(e));
     if (N) {
         if (cudaMalloc(&bt->tables, h.size() * 8) != cudaSuccess) {
             cudaGetLastError();
@@ -922,8 +984,14 @@ extern "C" tc_status tc_batch_run(tc_ctx* ctx, const tc_batch* bt, const uint32_
     cudaStream_t st = (cudaStream_t)stream;
     for (const auto& z : bt->zeros) CK(cudaMemsetAsync(OUT + z.first, 0, (size_t)z.second * 4, st));
     const size_t N = bt->total;
-    for (const auto& c : bt->classes) {
-        char* base = bt->scratch;
+    // the classes are independent: each on the next stream of the fan (largest first)
+    tc::StreamFan& fan = const_cast<tc::StreamFan&>(bt->fan);
+    const bool fanned = fan.ready;
+    if (fanned) CK(fan.fork(st));
+    for (size_t ci = bt->classes.size(); ci-- > 0;) {
+        const auto& c = bt->classes[ci];
+        const cudaStream_t cs = fanned ? fan.s[(bt->classes.size() - 1 - ci) % StreamFan::K] : st;
+        char* base = bt->scratch + c.off;
         u32* rA = (u32*)(base + c.L.total);
         u32* rB = (u32*)((char*)rA + align256(c.cnt * c.s * 4));
         u32* rO = (u32*)((char*)rB + align256(c.cnt * c.s * 4));
@@ -936,22 +1004,23 @@ extern "C" tc_status tc_batch_run(tc_ctx* ctx, const tc_batch* bt, const uint32_
         for (size_t c0 = 0; c0 < c.cnt; c0 += 65535) {
             const int cc = (int)std::min<size_t>(65535, c.cnt - c0);
             dim3 grid((unsigned)std::min<size_t>((c.s + 255) / 256, 64), cc);
-            gather_rows<<<grid, 256, 0, st>>>(A, aoff + c0, alen + c0, (int)c.s, rA + c0 * c.s, cc);
-            gather_rows<<<grid, 256, 0, st>>>(Bv, boff + c0, blen + c0, (int)c.s, rB + c0 * c.s, cc);
+            gather_rows<<<grid, 256, 0, cs>>>(A, aoff + c0, alen + c0, (int)c.s, rA + c0 * c.s, cc);
+            gather_rows<<<grid, 256, 0, cs>>>(Bv, boff + c0, blen + c0, (int)c.s, rB + c0 * c.s, cc);
         }
         CK(cudaGetLastError());
         // no context: no phase events and no host read-back inside a possibly captured run
         tc_status e = run_uniform(c.L, base, c.cnt, c.s, rA, (long)c.s, rB, (long)c.s, rO,
-                                  (long)(2 * c.s), false, st, nullptr, bt->err_dev);
+                                  (long)(2 * c.s), false, cs, nullptr, bt->err_dev);
         if (e) return e;
         for (size_t c0 = 0; c0 < c.cnt; c0 += 65535) {
             const int cc = (int)std::min<size_t>(65535, c.cnt - c0);
             dim3 grid((unsigned)std::min<size_t>((2 * c.s + 255) / 256, 64), cc);
-            scatter_rows<<<grid, 256, 0, st>>>(rO + c0 * 2 * c.s, (int)(2 * c.s), ooff + c0,
+            scatter_rows<<<grid, 256, 0, cs>>>(rO + c0 * 2 * c.s, (int)(2 * c.s), ooff + c0,
                                                olen + c0, OUT, cc);
         }
         CK(cudaGetLastError());
     }
+    if (fanned) CK(fan.join(st));
     return TC_OK;
 }
 
@@ -995,6 +1064,7 @@ extern "C" void tc_batch_destroy(tc_batch* bt) {
     int cur = 0;
     cudaGetDevice(&cur);
     cudaSetDevice(bt->device);
+    bt->fan.destroy();
     if (bt->tables) cudaFree(bt->tables);
     if (bt->scratch) cudaFree(bt->scratch);
     if (bt->err_dev) cudaFree(bt->err_dev);

@@ -46,6 +46,21 @@ cudaError_t launch_or_error(int* sticky, const int* word, cudaStream_t st);
 
 // Padded balanced length class of an operand length (at most 50% padding).
 size_t size_class(size_t L);
+
+// Independent work on several streams: fork() makes every stream of the fan wait
+// for the work enqueued so far on `st`, join() makes `st` wait for every stream
+// of the fan.  Events only, so a fork/join inside a stream capture becomes
+// parallel branches of the graph.
+struct StreamFan {
+    static constexpr int K = 8;
+    cudaStream_t s[K] = {};
+    cudaEvent_t fork_ev = nullptr, join_ev[K] = {};
+    bool ready = false;
+    cudaError_t init();
+    void destroy();
+    cudaError_t fork(cudaStream_t st);
+    cudaError_t join(cudaStream_t st);
+};
 }  // namespace tc
 
 struct tc_ctx {
@@ -63,6 +78,7 @@ struct tc_ctx {
     size_t pin_bytes[2] = {0, 0};
     cudaEvent_t pin_ev[2] = {nullptr, nullptr};
     int pin_turn = 0;
+    tc::StreamFan fan;          // size classes of tc_mul_batch run concurrently on these
     tc::Server* server = nullptr;
     // phase timing (tc_profile_enable)
     bool profile = false;
