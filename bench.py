@@ -79,6 +79,9 @@ def parse():
     p.add_argument("--reps", type=int, default=3, help="--case: timed repetitions")
     p.add_argument("--method", choices=["newton", "matrix"], default="newton",
                    help="--case interp: even-odd Newton route or inverse-Vandermonde matrix")
+    p.add_argument("--leaf", choices=["karatsuba", "schoolbook"], default="schoolbook",
+                   help="--case leaf: base-case variant of the lane-pair kernel (karatsuba: "
+                        "the in-kernel Karatsuba level from 49 limbs on)")
     return p.parse_args()
 
 
@@ -625,7 +628,10 @@ def run_case(args):
         count, L = args.count or 157320, args.limbs if args.limbs != LIMBS else 184
         A, B = _rand_dev(torch, (count, L), 1), _rand_dev(torch, (count, L), 2)
         OUT = torch.empty((count, 2 * L), dtype=torch.int32, device="cuda")
+        tc.tc_set_leaf_karatsuba(49 if args.leaf == "karatsuba" else 0)
         ms = _time_case(torch, lambda: tc.tc_schoolbook(A, B, OUT), args.reps)
+        tc.tc_set_leaf_karatsuba(tc.TC_LEAF_KARATSUBA_DEFAULT)
+        res["leaf"] = args.leaf
     elif args.case == "ntt":
         count, L = args.count or 1, args.limbs
         A, B = _rand_dev(torch, (count, L), 1), _rand_dev(torch, (count, L), 2)

@@ -449,6 +449,20 @@ tc_status tc_peak_madc(int blocks, int iters, uint32_t *sink, void *stream, doub
  */
 tc_status tc_test_bounded_waits(int polls, int withhold);
 
+/*
+ * Base-case variant (tuning and test hook; the paper has none).  The
+ * lane-pair base case (4096 or more products of up to 792 limbs) runs one
+ * Karatsuba level inside the kernel (Section 1's B = 2 split taken below the
+ * Toom threshold: three products of half-length rows instead of one) for rows
+ * of at least `min_limbs` limbs; 0 turns it off.  Both variants give the same
+ * limbs.  The default, TC_LEAF_KARATSUBA_DEFAULT, is where it measured faster
+ * on GB300.  Process-wide, from the next launch on; not for concurrent use
+ * with other work.  TC_EINVAL if min_limbs < 0 or 0 < min_limbs < 49 (the split
+ * needs seven 8-limb tiles).
+ */
+#define TC_LEAF_KARATSUBA_DEFAULT 384
+tc_status tc_set_leaf_karatsuba(int min_limbs);
+
 /* Message for a status code (static string). */
 const char *tc_strerror(tc_status s);
 

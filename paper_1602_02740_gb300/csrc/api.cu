@@ -233,7 +233,7 @@ tc_status run_uniform(const BatchLayout& L, char* base, size_t count, size_t s, 
     PhaseTimer pt{ctx, st};
     const int D = (int)L.g.size();
     if (D == 0) {
-        pt.begin(1, 0, 4.0 * count * 4 * s, (double)count * s * s);
+        pt.begin(1, 0, 4.0 * count * 4 * s, leaf_limb_products(s, count));
         if (L.base == TC_BASE_NTT)
             CK(launch_ntt_mul(A, lda, square ? A : Bm, square ? lda : ldb, OUT, ldo, (int)s,
                               (long)count, square, base + L.ntt, st));
@@ -274,7 +274,7 @@ tc_status run_uniform(const BatchLayout& L, char* base, size_t count, size_t s, 
         }
     }
     const LevelGeom& gl = L.g[D - 1];
-    pt.begin(1, D, 4.0 * L.P[D] * 4 * gl.e, (double)L.P[D] * gl.e * gl.e);
+    pt.begin(1, D, 4.0 * L.P[D] * 4 * gl.e, leaf_limb_products(gl.e, L.P[D]));
     if (L.base == TC_BASE_NTT)
         CK(launch_ntt_mul(inU, strU, inV, strV, reinterpret_cast<u32*>(base + L.prod[D - 1]),
                           gl.ystride, gl.e, L.P[D], square, base + L.ntt, st));

@@ -19,6 +19,7 @@
 // blocks per output limb and resolves carries with the warp scans.
 #include <mutex>
 
+#include "../../include/tc.h"
 #include "tc_device.cuh"
 #include "tc_internal.h"
 
@@ -395,7 +396,28 @@ cudaError_t launch_schoolbook_big(const u32* A, long lda, const u32* Bm, long ld
 // diagonal tile the even/odd rows keep columns c > row) and doubles at
 // emission, adding a_i^2 on the even columns.
 // ---------------------------------------------------------------------------
+//
+// One Karatsuba level inside the kernel (rows of at least g_kara_min_limbs
+// limbs, 384 by default: measured on GB300 it is 4 % faster at 456 limbs and
+// 10 % at 792, but slower at 234 and below, where the three sweeps' extra
+// diagonals cost more than the 23 % of tiles they save).  With a = a0 + a1 X, b = b0 + b1 X, X = 2^(32k), k = 8 ceil(T/2):
+//   P0 = a0 b0, P2 = a1 b1, P1 = |a0 - a1| |b0 - b1|,
+//   a b = P0 + (P0 + P2 - s P1) X + P2 X^2,  s = sign((a0 - a1)(b0 - b1)),
+// three sub-products of ceil(T/2)^2, floor(T/2)^2 and ceil(T/2)^2 tiles instead
+// of T^2 (177 instead of 225 at 15 tiles).  The lane pair runs the same
+// diagonal sweep three times: P0 into columns [0, 2k) and P2 into [2k, 2s) of
+// the output row (disjoint, plain stores); then the differences overwrite a0
+// and b0 in shared memory (one lane each), and with H0 = P0 div X and
+// L2 = P2 mod X the even lane forms T = H0 + L2 and stores it over both.
+// Splitting P0 = L0 + H0 X, P2 = L2 + H2 X, P1 = L1 + H1 X, the product is
+//   L0 + (T + L0 - s L1) X + (T + H2 - s H1) X^2 + H2 X^3,
+// so the third sweep, over the windows of P1, adds T (already in place) plus
+// L0 or H2 (untouched rows of the output) and subtracts or adds its own window,
+// with a signed carry from window to window; the last carry ripples into H2's
+// columns.  Every window of the combine is read and written once.
+// ---------------------------------------------------------------------------
 constexpr int PAIR_WARPS = 2;
+constexpr int PAIR_KARA_MIN_LIMBS = 49;  // from 7 tiles on, 2s >= 3k holds
 
 __host__ __device__ inline int pair_stride(int s) {
     int sp = (s + 7) / 8 * 8;  // a multiple of 8 words: 8 or 24 (mod 32) wanted
@@ -489,6 +511,85 @@ __device__ __forceinline__ void double_add_squares(u32* R, const u32* a) {
         : "r"(S[0]), "r"(S[1]), "r"(S[2]), "r"(S[3]), "r"(S[4]), "r"(S[5]), "r"(S[6]), "r"(S[7]));
 }
 
+// Eight limbs of an output row at pos (zeros at and past len), for a window
+// the emission reads later in the same diagonal.  The loads are volatile with a
+// memory clobber so that they stay at this point of the diagonal: hoisted to
+// the top of the unrolled diagonals they would hold three windows' registers.
+__device__ __forceinline__ void prefetch8(const u32* row, int pos, int len, bool vec, u32 v[8]) {
+    if (vec && pos + 8 <= len) {
+        asm volatile("ld.global.v4.u32 {%0, %1, %2, %3}, [%8];\n\t"
+                     "ld.global.v4.u32 {%4, %5, %6, %7}, [%8+16];"
+                     : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                       "=r"(v[7])
+                     : "l"(row + pos)
+                     : "memory");
+    } else {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            u32 x = 0;
+            if (pos + k < len) asm volatile("ld.global.u32 %0, [%1];" : "=r"(x) : "l"(row + pos + k) : "memory");
+            v[k] = x;
+        }
+    }
+}
+
+// Karatsuba combine of one window: res = tw + xw + (sub ? -R : R) + carry over
+// eight limbs; carry (signed, |carry| <= 3) becomes the window's overflow.
+// -R is ~R + 1 - 2^256, so one add chain with carry-in (sub & 1) serves both
+// signs; a negative incoming carry enters as its 256-bit two's complement.
+__device__ __forceinline__ void combine_window(const u32 tw[8], const u32 xw[8], const u32 R[8], u32 sub,
+                                               int& carry, u32 res[8]) {
+    u32 S[8], Rm[8];
+    u32 c = add4c(tw, xw, 0u, S);
+    c = add4c(tw + 4, xw + 4, c, S + 4);
+    int top = (int)c - (int)(sub & 1u);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) Rm[j] = R[j] ^ sub;
+    c = add4c(S, Rm, sub & 1u, res);
+    c = add4c(S + 4, Rm + 4, c, res + 4);
+    top += (int)c;
+    const u32 ext = carry < 0 ? ~0u : 0u;
+    u32 co;
+    asm("add.cc.u32 %0, %0, %9;\n\t"
+        "addc.cc.u32 %1, %1, %10;\n\t"
+        "addc.cc.u32 %2, %2, %10;\n\t"
+        "addc.cc.u32 %3, %3, %10;\n\t"
+        "addc.cc.u32 %4, %4, %10;\n\t"
+        "addc.cc.u32 %5, %5, %10;\n\t"
+        "addc.cc.u32 %6, %6, %10;\n\t"
+        "addc.cc.u32 %7, %7, %10;\n\t"
+        "addc.u32 %8, 0, 0;"
+        : "+r"(res[0]), "+r"(res[1]), "+r"(res[2]), "+r"(res[3]), "+r"(res[4]), "+r"(res[5]),
+          "+r"(res[6]), "+r"(res[7]), "=r"(co)
+        : "r"((u32)carry), "r"(ext));
+    carry = top + (int)co - (carry < 0 ? 1 : 0);
+}
+
+// r[0, k) = |r[0, k) - r[k, k + n1)| in place (the second operand is zero past
+// n1 <= k; k and n1 multiples of 4, r 16-byte aligned shared memory); returns 1
+// when the difference was negative.
+__device__ __forceinline__ u32 abs_diff_inplace(u32* r, int k, int n1) {
+    u32 br = 0;
+    for (int i = 0; i < k; i += 4) {
+        const uint4 x = ld4(r + i);
+        const uint4 y = i < n1 ? ld4(r + k + i) : make_uint4(0u, 0u, 0u, 0u);
+        const u32 xa[4] = {x.x, x.y, x.z, x.w}, ya[4] = {y.x, y.y, y.z, y.w};
+        u32 d[4];
+        br = sub4b(xa, ya, br, d);
+        st4(r + i, d);
+    }
+    if (br) {  // negate: ~d + 1
+        u32 c = 1;
+        for (int i = 0; i < k; i += 4) {
+            const uint4 x = ld4(r + i);
+            u32 d[4] = {~x.x, ~x.y, ~x.z, ~x.w};
+            c = inc4(d, c);
+            st4(r + i, d);
+        }
+    }
+    return br;
+}
+
 // One anti-diagonal of the pair kernel; OFF is the ring offset of the window's
 // column 0 among the twelve accumulator slots (slot (OFF + k) mod 12 holds
 // column 8D + 4h + k).
@@ -500,11 +601,28 @@ struct PairDiag {
     int T, h;
     bool emit, aligned;
     int out_len;
+    // Karatsuba sweeps (out = the product row, out_len = 2s): mode 1 is P2,
+    // whose windows land on columns 2k + 8D and whose low half L2 becomes
+    // T = H0 + L2 on the fly (stored at k + 8D and 2k + 8D); mode 2 is the
+    // combine of P1's windows into columns k + 8D (see combine_window).
+    int mode;
+    int ks, T0;   // split column k and tiles of a0
+    u32 sub;      // all ones: the middle product is subtracted
+    int carry;    // mode 1: T's carry chain; mode 2: signed carry between windows
+    int cT;       // carry out of T
 
     template <int OFF>
     __device__ __forceinline__ void step(int D, u32 (&lo)[12], u32 (&mid)[12], u32 (&hi)[12],
-                                         u32 (&cin)[3]) const {
+                                         u32 (&cin)[3]) {
         auto S = [](int k) { return (OFF + k) % 12; };
+        // the output windows this diagonal's emission reads, loaded ahead of its
+        // products so that their latency overlaps them
+        u32 pa[8] = {0, 0, 0, 0, 0, 0, 0, 0}, pb[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        if (mode == 1 && emit && D < T0) prefetch8(out, ks + 8 * D, out_len, aligned, pa);      // H0
+        if (mode == 2 && emit) {
+            prefetch8(out, ks + 8 * D, out_len, aligned, pa);                                   // T
+            prefetch8(out, D < T0 ? 8 * D : 2 * ks + 8 * D, out_len, aligned, pb);              // L0, H2
+        }
         const int Ilo = D - T + 1 > 0 ? D - T + 1 : 0;
         int Ihi = D < T - 1 ? D : T - 1;
         if (SQ && Ihi > D / 2) Ihi = D / 2;
@@ -554,14 +672,38 @@ struct PairDiag {
             add96(lo[S(8)], mid[S(8)], hi[S(8)], R[8], R[9], R[10]);
         }
         if (emit) {
-            const int c0 = 8 * D;
-            if (aligned && c0 + 8 <= out_len) {
-                st4(out + c0, R);
-                st4(out + c0 + 4, R + 4);
-            } else {
+            // whole windows below 3k <= 2s: the T windows and the combined ones
+            auto put8 = [&](u32* dst, const u32* v) {
+                if (aligned) {
+                    st4(dst, v);
+                    st4(dst + 4, v + 4);
+                } else {
 #pragma unroll
-                for (int k = 0; k < 8; ++k)
-                    if (c0 + k < out_len) out[c0 + k] = R[k];
+                    for (int j = 0; j < 8; ++j) dst[j] = v[j];
+                }
+            };
+            if (mode == 2) {
+                if (D == T0) carry += cT;
+                u32 res[8];
+                combine_window(pa, pb, R, sub, carry, res);
+                put8(out + ks + 8 * D, res);
+            } else if (mode == 1 && D < T0) {
+                u32 t[8];
+                u32 c = add4c(pa, R, (u32)carry, t);
+                carry = (int)add4c(pa + 4, R + 4, c, t + 4);
+                put8(out + ks + 8 * D, t);
+                put8(out + 2 * ks + 8 * D, t);
+                if (D == T0 - 1) cT = carry;
+            } else {
+                const int c0 = (mode == 1 ? 2 * ks : 0) + 8 * D;
+                if (aligned && c0 + 8 <= out_len) {
+                    st4(out + c0, R);
+                    st4(out + c0 + 4, R + 4);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 8; ++k)
+                        if (c0 + k < out_len) out[c0 + k] = R[k];
+                }
             }
         }
         // columns 0..7 are done: their slots become columns 4..11 of the next window
@@ -570,7 +712,7 @@ struct PairDiag {
     }
 };
 
-template <bool SQ>
+template <bool SQ, bool KARA>
 __global__ void __launch_bounds__(32 * PAIR_WARPS)
 leaf_pair_kernel(const u32* __restrict__ A, long lda, const u32* __restrict__ Bm, long ldb,
                  u32* __restrict__ OUT, long ldo, int s, long P, int vec) {
@@ -628,22 +770,53 @@ leaf_pair_kernel(const u32* __restrict__ A, long lda, const u32* __restrict__ Bm
     const u32* rb = sb + q * sp;
     u32* out = OUT + (p < P ? p : 0) * ldo;
     const bool aligned = ((reinterpret_cast<uintptr_t>(out) & 15u) == 0);
-    const int out_len = 2 * s;
-    u32 lo[12], mid[12], hi[12], cin[3] = {0, 0, 0};
+    // Karatsuba: a0 = the first T0 tiles of a row, a1 = the other T - T0
+    const int T0 = KARA ? (T + 1) / 2 : T, k = 8 * T0;
+    PairDiag<SQ> pd{ra, rb, out, T0, h, emit, aligned, 2 * s, 0, k, T0, 0u, 0, 0};
+#pragma unroll 1
+    for (int part = 0; part < (KARA ? 3 : 1); ++part) {
+        if (KARA && part == 1) {          // P2 = a1 b1 -> columns [2k, 2s), T = H0 + L2
+            pd.ra = ra + k;
+            pd.rb = rb + k;
+            pd.T = T - T0;
+            pd.mode = 1;
+        } else if (KARA && part == 2) {   // P1 = |a0 - a1| |b0 - b1|, combined
+            __syncwarp();
+            u32 neg = 0;
+            if (!SQ || h == 0) neg = abs_diff_inplace(const_cast<u32*>(h == 0 ? ra : rb), k, 8 * (T - T0));
+            const u32 other = __shfl_xor_sync(FULL, neg, 1);
+            pd.sub = (SQ || neg == other) ? ~0u : 0u;
+            __syncwarp();
+            pd.ra = ra;
+            pd.rb = rb;
+            pd.T = T0;
+            pd.mode = 2;
+            pd.carry = 0;
+        }
+        u32 lo[12], mid[12], hi[12], cin[3] = {0, 0, 0};
 #pragma unroll
-    for (int k = 0; k < 12; ++k) { lo[k] = 0; mid[k] = 0; hi[k] = 0; }
-    // The twelve slots are a ring that advances by eight per diagonal, so three
-    // consecutive diagonals (ring offsets 0, 8, 4) run unrolled with fixed
-    // register names instead of moving the window.
-    PairDiag<SQ> pd{ra, rb, out, T, h, emit, aligned, 2 * s};
-    int D = 0;
-    for (; D + 3 <= 2 * T; D += 3) {
-        pd.template step<0>(D, lo, mid, hi, cin);
-        pd.template step<8>(D + 1, lo, mid, hi, cin);
-        pd.template step<4>(D + 2, lo, mid, hi, cin);
+        for (int j = 0; j < 12; ++j) { lo[j] = 0; mid[j] = 0; hi[j] = 0; }
+        // The twelve slots are a ring that advances by eight per diagonal, so three
+        // consecutive diagonals (ring offsets 0, 8, 4) run unrolled with fixed
+        // register names instead of moving the window.
+        const int TT = pd.T;
+        int D = 0;
+        for (; D + 3 <= 2 * TT; D += 3) {
+            pd.template step<0>(D, lo, mid, hi, cin);
+            pd.template step<8>(D + 1, lo, mid, hi, cin);
+            pd.template step<4>(D + 2, lo, mid, hi, cin);
+        }
+        if (D < 2 * TT) pd.template step<0>(D++, lo, mid, hi, cin);
+        if (D < 2 * TT) pd.template step<8>(D++, lo, mid, hi, cin);
     }
-    if (D < 2 * T) pd.template step<0>(D++, lo, mid, hi, cin);
-    if (D < 2 * T) pd.template step<8>(D++, lo, mid, hi, cin);
+    if (KARA && emit) {  // the last window's carry and T's second carry into H2's columns
+        int c = pd.carry + pd.cT;
+        for (int i = 3 * k; i < 2 * s && c != 0; ++i) {
+            const long long v = (long long)out[i] + c;
+            out[i] = (u32)v;
+            c = (int)(v >> 32);
+        }
+    }
 }
 
 // Products at or above this count use the lane-per-product kernels: a lane
@@ -651,6 +824,26 @@ leaf_pair_kernel(const u32* __restrict__ A, long lda, const u32* __restrict__ Bm
 // else one lane per product reading its rows from global memory.
 constexpr long LANE_KERNEL_MIN = 4096;
 constexpr size_t PAIR_SMEM_MAX = 200 * 1024;
+
+static int g_kara_min_limbs = TC_LEAF_KARATSUBA_DEFAULT;   // tc_set_leaf_karatsuba
+
+static bool pair_karatsuba(int s) {
+    const int T = (s + 7) / 8, k = 8 * ((T + 1) / 2);
+    return g_kara_min_limbs > 0 && s >= g_kara_min_limbs && s >= PAIR_KARA_MIN_LIMBS && 2 * s >= 3 * k;
+}
+
+static bool pair_kernel_fits(int s, bool square) {
+    return (size_t)(square ? 1 : 2) * 16 * pair_stride(s) * 4 * PAIR_WARPS <= PAIR_SMEM_MAX;
+}
+
+double leaf_limb_products(int s, long P) {
+    if (P >= LANE_KERNEL_MIN && pair_kernel_fits(s, false) && pair_karatsuba(s)) {
+        const double k = 8.0 * (((s + 7) / 8 + 1) / 2);
+        return (double)P * (2.0 * k * k + (s - k) * (s - k));
+    }
+    return (double)P * s * s;
+}
+
 
 cudaError_t launch_leaf(const u32* A, long lda, const u32* Bm, long ldb, u32* OUT, long ldo,
                         int s, long P, cudaStream_t st) {
@@ -663,18 +856,25 @@ cudaError_t launch_leaf(const u32* A, long lda, const u32* Bm, long ldb, u32* OU
         if (per_warp * PAIR_WARPS <= PAIR_SMEM_MAX) {
             static std::once_flag pair_once;
             std::call_once(pair_once, [] {
-                cudaFuncSetAttribute(leaf_pair_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, PAIR_SMEM_MAX);
-                cudaFuncSetAttribute(leaf_pair_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, PAIR_SMEM_MAX);
+                cudaFuncSetAttribute(leaf_pair_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, PAIR_SMEM_MAX);
+                cudaFuncSetAttribute(leaf_pair_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, PAIR_SMEM_MAX);
+                cudaFuncSetAttribute(leaf_pair_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, PAIR_SMEM_MAX);
+                cudaFuncSetAttribute(leaf_pair_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, PAIR_SMEM_MAX);
             });
             const unsigned grid = (unsigned)((P + 16 * PAIR_WARPS - 1) / (16 * PAIR_WARPS));
             const size_t smem = per_warp * PAIR_WARPS;
+            const bool kara = pair_karatsuba(s);
+#define TC_PAIR_LAUNCH(SQ_, K_)                                                                        \
+    do {                                                                                               \
+        note_kernel("leaf_pair_kernel<" #SQ_ ", " #K_ ">");                                            \
+        leaf_pair_kernel<SQ_, K_><<<grid, 32 * PAIR_WARPS, smem, st>>>(A, lda, Bm, ldb, OUT, ldo, s, P, vec); \
+    } while (0)
             if (square) {
-                note_kernel("leaf_pair_kernel<true>");
-                leaf_pair_kernel<true><<<grid, 32 * PAIR_WARPS, smem, st>>>(A, lda, Bm, ldb, OUT, ldo, s, P, vec);
+                if (kara) TC_PAIR_LAUNCH(true, true); else TC_PAIR_LAUNCH(true, false);
             } else {
-                note_kernel("leaf_pair_kernel<false>");
-                leaf_pair_kernel<false><<<grid, 32 * PAIR_WARPS, smem, st>>>(A, lda, Bm, ldb, OUT, ldo, s, P, vec);
+                if (kara) TC_PAIR_LAUNCH(false, true); else TC_PAIR_LAUNCH(false, false);
             }
+#undef TC_PAIR_LAUNCH
             return cudaGetLastError();
         }
         const unsigned grid = (unsigned)((P + 127) / 128);
@@ -707,3 +907,9 @@ cudaError_t launch_leaf(const u32* A, long lda, const u32* Bm, long ldb, u32* OU
 }
 
 }  // namespace tc
+
+extern "C" tc_status tc_set_leaf_karatsuba(int min_limbs) {
+    if (min_limbs < 0 || (min_limbs > 0 && min_limbs < tc::PAIR_KARA_MIN_LIMBS)) return TC_EINVAL;
+    tc::g_kara_min_limbs = min_limbs;
+    return TC_OK;
+}

@@ -33,6 +33,9 @@ constexpr int LEAF_MAX = 1024;
 
 cudaError_t launch_leaf(const uint32_t* A, long lda, const uint32_t* Bm, long ldb,
                         uint32_t* OUT, long ldo, int s, long P, cudaStream_t st);
+// Limb products launch_leaf performs for P products of s limbs (s^2 each, or
+// 2k^2 + (s - k)^2 with the in-kernel Karatsuba level).
+double leaf_limb_products(int s, long P);
 
 // Plain schoolbook of any operand length (column sums in `cols`, see below).
 size_t schoolbook_big_bytes(int s, long P);

@@ -70,6 +70,7 @@ _SIGS = {
     "tc_destroy": (None, [_vp]),
     "tc_check": (ctypes.c_int, [_vp, _vp]),
     "tc_test_bounded_waits": (ctypes.c_int, [ctypes.c_int, ctypes.c_int]),
+    "tc_set_leaf_karatsuba": (ctypes.c_int, [ctypes.c_int]),
     "tc_plan_for": (ctypes.c_int, [_vp, _sz, _optp]),
     "tc_scratch_bytes": (ctypes.c_int, [_vp, _sz, _sz, _optp, ctypes.POINTER(ctypes.c_size_t)]),
     "tc_mul": (ctypes.c_int, [_vp, _u32p, _sz, _u32p, _sz, _u32p, _optp, _vp]),
@@ -584,3 +585,13 @@ def tc_test_bounded_waits(polls: int, withhold: bool):
     """Test hook: shorten the segment-parallel passes' bounded waits to `polls`
     polls (0 = default) and, if `withhold`, make the waits run out."""
     _check(lib().tc_test_bounded_waits(int(polls), 1 if withhold else 0), "tc_test_bounded_waits")
+
+
+TC_LEAF_KARATSUBA_DEFAULT = 384
+
+
+def tc_set_leaf_karatsuba(min_limbs: int):
+    """Base-case variant: one Karatsuba level inside the lane-pair kernel for
+    rows of at least `min_limbs` limbs (0: never; default 384); the same limbs
+    either way."""
+    _check(lib().tc_set_leaf_karatsuba(int(min_limbs)), "tc_set_leaf_karatsuba")

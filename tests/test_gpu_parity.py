@@ -471,6 +471,54 @@ def test_square_lane_kernel(tc, L):
         assert np.array_equal(out[k], native.schoolbook(A[k], A[k])), (L, k)
 
 
+def _karatsuba_rows(count, L, seed):
+    """Operand rows that reach every sign case of the in-kernel Karatsuba level
+    (a = a0 + a1 X with a0 the first 8 ceil(T/2) limbs): a0 above, below and
+    equal to a1, a zero half, all-ones rows, then uniform rows."""
+    k = 8 * (((L + 7) // 8 + 1) // 2)
+    g = inputs.rng(seed)
+    A = g.integers(0, 1 << 32, size=(count, L), dtype=np.uint64).astype(np.uint32)
+    B = g.integers(0, 1 << 32, size=(count, L), dtype=np.uint64).astype(np.uint32)
+    n1 = L - k
+    A[0] = 0xFFFFFFFF; B[0] = 0xFFFFFFFF              # a0 > a1 (a1 shorter)
+    A[1, :k] = 0; B[1, :k] = 0                        # a0 < a1, b0 < b1: P1 subtracted
+    A[2, :k] = 0                                      # a0 < a1, b0 > b1 likely: added
+    A[3, :n1] = A[3, k:]; A[3, n1:k] = 0              # a0 == a1: zero difference
+    B[3, :n1] = B[3, k:]; B[3, n1:k] = 0
+    A[4, k:] = 0                                      # a1 = 0
+    B[5] = 0                                          # a zero operand
+    A[6, :k] = 0xFFFFFFFF; A[6, k:] = 0xFFFFFFFF; B[6, :k] = 1; B[6, k:] = 0xFFFFFFFF
+    A[7, n1:k] = 0; A[7, :n1] = A[7, k:]; A[7, 0] ^= 1    # a0, a1 differ in one low bit
+    return A, B
+
+
+@pytest.mark.parametrize("L", [48, 49, 56, 57, 64, 100, 116, 120, 121, 184, 224, 255, 792])
+@pytest.mark.parametrize("square", [False, True])
+def test_karatsuba_base_case(tc, L, square):
+    """The lane-pair base case with its Karatsuba level forced on from 49 limbs
+    against the oracle's schoolbook on every row (sampled rows at 792 limbs),
+    and the plain variant of the same kernel on the same rows."""
+    t = tc.tc
+    count = 4100
+    A, B = _karatsuba_rows(count, L, 7000 + L)
+    if square:
+        B = A
+    dA = dev(A)
+    dB = dA if square else dev(B)
+    try:
+        t.tc_set_leaf_karatsuba(49)
+        got = host(t.tc_schoolbook(dA, dB))
+        t.tc_set_leaf_karatsuba(0)
+        plain = host(t.tc_schoolbook(dA, dB))
+    finally:
+        t.tc_set_leaf_karatsuba(t.TC_LEAF_KARATSUBA_DEFAULT)
+    rows = range(count) if L <= 256 else list(range(0, count, 41)) + list(range(8)) + [count - 1]
+    for r in rows:
+        want = native.schoolbook(A[r], B[r])
+        assert np.array_equal(got[r], want), (L, r, square)
+        assert np.array_equal(plain[r], want), (L, r, square, "plain")
+
+
 # ---------------------------------------------------------------- many small interpolations
 # 2048 or more products with small values select the warp-per-product kernel.
 
@@ -503,6 +551,37 @@ def test_interpolate_many_products(tc, B, L):
             S[k, p] = 1 if val < 0 else 0
     out = host(tc.tc.tc_toom_interpolate(dev(Y), L, B, SGN_U=torch.from_numpy(S).cuda()))
     for k in check:
+        assert same_limbs(out[k], to_int(A[k]) * to_int(Bm[k])), (B, L, k)
+
+
+# Large batches of low degree, every product checked: 16 400 products (a grid of
+# 513 blocks of 32 warps for the warp-per-product kernels); (4, 457) is the 2^20-bit
+# benchmark's level-2 shape; ragged top blocks except for (2, 16), (3, 24), (4, 32).
+@pytest.mark.parametrize("B,L", [(2, 16), (2, 101), (3, 24), (3, 100), (4, 32), (4, 259),
+                                 (4, 457), (4, 1000)])
+def test_interpolate_large_batch_low_degree(tc, B, L):
+    import torch
+    count = 16400
+    _, e, _, ystride = tc.tc.level_sizes(L, B)
+    g = inputs.rng(11 * B + L)
+    A = g.integers(0, 1 << 32, size=(count, L), dtype=np.uint64).astype(np.uint32)
+    Bm = g.integers(0, 1 << 32, size=(count, L), dtype=np.uint64).astype(np.uint32)
+    b = toom.ceil_div(L, B)
+    A[1] = 0xFFFFFFFF; Bm[1] = 0xFFFFFFFF              # largest values
+    A[2] = 0                                            # a zero operand
+    A[3, :] = 0; A[3, b:min(2 * b, L)] = 0xFFFFFFFF     # odd block only: negative values at -x
+    Bm[3, b:] = 0                                       # ... times block 0 alone
+    A[4] = inputs.sparse(L, 5)
+    Y = np.zeros((count, 2 * B - 1, ystride), dtype=np.uint32)
+    S = np.zeros((count, 2 * B - 1), dtype=np.uint8)
+    for k in range(count):
+        y = _oracle_level(to_int(A[k]), to_int(Bm[k]), L, B)
+        for p, val in enumerate(y):
+            Y[k, p, :2 * e] = from_int(abs(val), 2 * e)
+            S[k, p] = 1 if val < 0 else 0
+    assert S[3].any()
+    out = host(tc.tc.tc_toom_interpolate(dev(Y), L, B, SGN_U=torch.from_numpy(S).cuda()))
+    for k in range(count):
         assert same_limbs(out[k], to_int(A[k]) * to_int(Bm[k])), (B, L, k)
 
 

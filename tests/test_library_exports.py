@@ -75,6 +75,19 @@ def test_host_argument_checks_without_gpu(libtc):
     libtc.tc_batch_destroy(None)
 
 
+def test_leaf_karatsuba_threshold_checked_on_the_host(libtc):
+    """The base-case variant setting: 0 (off) or a row length the split can
+    take (49 limbs and up); anything else is TC_EINVAL."""
+    libtc.tc_set_leaf_karatsuba.argtypes = [ctypes.c_int]
+    try:
+        assert libtc.tc_set_leaf_karatsuba(-1) == -1
+        assert libtc.tc_set_leaf_karatsuba(48) == -1
+        assert libtc.tc_set_leaf_karatsuba(0) == 0
+        assert libtc.tc_set_leaf_karatsuba(49) == 0
+    finally:
+        assert libtc.tc_set_leaf_karatsuba(384) == 0
+
+
 def test_batch_tables_rejected_on_the_host(libtc):
     """Negative or huge offsets and lengths in a packed batch are rejected
     (TC_EINVAL) before the context is used or anything is launched."""
