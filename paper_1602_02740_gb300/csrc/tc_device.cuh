@@ -357,11 +357,68 @@ __device__ __forceinline__ bool ones_seg(const u32 r[KL]) {
     return x == FULL;
 }
 
-// Warp-wide add of two chunks of 32 KL limbs: each lane adds its KL limbs
-// with carry-in 0, the lanes' carries are resolved by one lookahead, and the
-// lanes that receive a carry increment their sum.
+// r += c (c in {0, 1}) / r -= c over KL limbs, returning the carry / borrow out.
+template <int KL>
+__device__ __forceinline__ u32 inc_seg_out(u32 r[KL], u32 c) {
+#pragma unroll
+    for (int j = 0; j < KL; j += 4) c = inc4(r + j, c);
+    return c;
+}
+
+template <int KL>
+__device__ __forceinline__ u32 dec_seg_out(u32 r[KL], u32 c) {
+#pragma unroll
+    for (int j = 0; j < KL; j += 4) c = dec4(r + j, c);
+    return c;
+}
+
+// Warp-wide add of two chunks of 32 KL limbs.  Each lane adds its KL limbs with
+// carry-in 0 and then adds the carry out of the lane below (lane 0: the chunk's
+// carry-in).  That is the whole carry unless a lane's sum was all ones and
+// received a carry, which passes it on; such lanes (probability 2^-32KL on
+// uniform data, but common in structured values) are resolved one lane per
+// round until none is left, at most 31 rounds.  A lane gives out at most one
+// carry in total: one that produced a carry itself is not all ones after its
+// carry-in.
 template <int KL>
 __device__ __forceinline__ void warp_add_seg(const u32 a[KL], const u32 b[KL], u32& carry, u32 r[KL]) {
+    const int lane = lane_id();
+    const u32 g = add_seg<KL>(a, b, 0u, r);
+    u32 cin = __shfl_up_sync(FULL, g, 1);
+    if (lane == 0) cin = carry;
+    u32 o = inc_seg_out<KL>(r, cin);
+    u32 out = g | o;
+    while (__any_sync(FULL, o)) {
+        u32 x = __shfl_up_sync(FULL, o, 1);
+        if (lane == 0) x = 0;
+        o = inc_seg_out<KL>(r, x);
+        out |= o;
+    }
+    carry = __shfl_sync(FULL, out, 31);
+}
+
+// The same for r = a - b with borrows (a propagating lane: difference 0).
+template <int KL>
+__device__ __forceinline__ void warp_sub_seg(const u32 a[KL], const u32 b[KL], u32& borrow, u32 r[KL]) {
+    const int lane = lane_id();
+    const u32 g = sub_seg<KL>(a, b, 0u, r);
+    u32 bin = __shfl_up_sync(FULL, g, 1);
+    if (lane == 0) bin = borrow;
+    u32 o = dec_seg_out<KL>(r, bin);
+    u32 out = g | o;
+    while (__any_sync(FULL, o)) {
+        u32 x = __shfl_up_sync(FULL, o, 1);
+        if (lane == 0) x = 0;
+        o = dec_seg_out<KL>(r, x);
+        out |= o;
+    }
+    borrow = __shfl_sync(FULL, out, 31);
+}
+
+// The same add and subtract with every lane's carry resolved by the lookahead
+// scan in one step (no data-dependent rounds).
+template <int KL>
+__device__ __forceinline__ void warp_add_seg_scan(const u32 a[KL], const u32 b[KL], u32& carry, u32 r[KL]) {
     const u32 g = add_seg<KL>(a, b, 0u, r);
     const bool p = !g && ones_seg<KL>(r);
     u32 cout;
@@ -371,7 +428,7 @@ __device__ __forceinline__ void warp_add_seg(const u32 a[KL], const u32 b[KL], u
 }
 
 template <int KL>
-__device__ __forceinline__ void warp_sub_seg(const u32 a[KL], const u32 b[KL], u32& borrow, u32 r[KL]) {
+__device__ __forceinline__ void warp_sub_seg_scan(const u32 a[KL], const u32 b[KL], u32& borrow, u32 r[KL]) {
     const u32 g = sub_seg<KL>(a, b, 0u, r);
     const bool p = !g && zero_seg<KL>(r);
     u32 bout;
@@ -380,8 +437,10 @@ __device__ __forceinline__ void warp_sub_seg(const u32 a[KL], const u32 b[KL], u
     borrow = bout;
 }
 
-// Two independent warp subtractions, interleaved step by step (more
-// independent instructions between the ballots of each).
+// Two independent warp subtractions with the lookahead scan, interleaved step by
+// step (the ballots of one between the instructions of the other).  The
+// latency-bound two-warp interpolation uses the scan forms throughout: there
+// they measured faster than the lane-by-lane rounds.
 template <int KL>
 __device__ __forceinline__ void warp_sub_seg2(const u32 a0[KL], const u32 b0[KL], u32& bor0, u32 r0[KL],
                                               const u32 a1[KL], const u32 b1[KL], u32& bor1, u32 r1[KL]) {

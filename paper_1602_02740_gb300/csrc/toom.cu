@@ -1611,8 +1611,8 @@ interp_split_kernel(InterpArgs a, DivTable dt, FinTable ft, long P) {
                     ld_seg_masked<KL>(yk + (2 * m + 2) * (long)g.ystride, base + KL * lane, len, qn);
                 }
                 u32 cb = s[0];
-                if ((p == 0) != neg) warp_add_seg<KL>(pv, qv, cb, r);
-                else warp_sub_seg<KL>(pv, qv, cb, r);
+                if ((p == 0) != neg) warp_add_seg_scan<KL>(pv, qv, cb, r);
+                else warp_sub_seg_scan<KL>(pv, qv, cb, r);
                 const bool right = p == 0 || m == 1;  // / 2 (else a left shift by m - 2)
                 if (right) {
                     u32 e[KL + 1];
@@ -1688,7 +1688,7 @@ interp_split_kernel(InterpArgs a, DivTable dt, FinTable ft, long P) {
                         st_seg<KL>(V(m), oa);
                         st_seg<KL>(V(mb), ob);
                     } else {
-                        warp_sub_seg<KL>(xa, za, bwa, dva);
+                        warp_sub_seg_scan<KL>(xa, za, bwa, dva);
                         look_behind<KL, 1>(dva, ha, ea);
 #pragma unroll
                         for (int j = 0; j < KL; ++j) oa[j] = fshr(ea[j], ea[j + 1], Ra);
@@ -1763,7 +1763,7 @@ interp_split_kernel(InterpArgs a, DivTable dt, FinTable ft, long P) {
                         st_seg<KL>(V(kx), ra);
                         st_seg<KL>(V(kx + 1), rb);
                     } else {
-                        warp_sub_seg<KL>(xa, sa, bwa, ra);
+                        warp_sub_seg_scan<KL>(xa, sa, bwa, ra);
                         st_seg<KL>(V(kx), ra);
                     }
                     __syncwarp();
