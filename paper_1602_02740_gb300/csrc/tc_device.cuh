@@ -158,6 +158,8 @@ struct UnsignedNorm {
     u32 carry;      // 0/1 carry into this chunk
 };
 
+__device__ __forceinline__ u32 inc4(u32* r, u32 c);  // r += c over 4 limbs, the carry out
+
 __device__ __forceinline__ void warp_norm_unsigned(const u64 cols[4], UnsignedNorm& st, u32 out[4]) {
     const int lane = lane_id();
     u64 c[4];
@@ -173,22 +175,28 @@ __device__ __forceinline__ void warp_norm_unsigned(const u64 cols[4], UnsignedNo
     y[0] = (u64)d[0] + prev_c;
 #pragma unroll
     for (int j = 1; j < 4; ++j) y[j] = (u64)d[j] + c[j - 1];
-    bool g = false, p = true;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const bool gj = (y[j] >> 32) != 0, pj = y[j] == 0xffffffffull;
-        g = gj || (pj && g);
-        p = pj && p;
-    }
-    u32 cout;
-    u32 x = warp_carry_scan(g, p, st.carry, &cout);
+    // the lane's digits with carry-in 0 (y < 2^33 - 1, so every carry is 0 or 1);
+    // then the carry out of the lane below, passed on only by an all-ones lane
+    // (a lane that carried out itself is at most 2^128 - 2 after it), one lane
+    // per round under a vote, as in warp_add_seg
+    u32 x = 0;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         const u64 v = y[j] + x;
         out[j] = (u32)v;
         x = (u32)(v >> 32);
     }
-    st.carry = cout;
+    u32 cin = __shfl_up_sync(FULL, x, 1);
+    if (lane == 0) cin = st.carry;
+    u32 o = inc4(out, cin);
+    u32 total = x | o;
+    while (__any_sync(FULL, o)) {
+        u32 t = __shfl_up_sync(FULL, o, 1);
+        if (lane == 0) t = 0;
+        o = inc4(out, t);
+        total |= o;
+    }
+    st.carry = __shfl_sync(FULL, total, 31);
     st.col_carry = __shfl_sync(FULL, c[3], 31);
 }
 

@@ -221,6 +221,15 @@ eval_kernel(const u32* __restrict__ in, long in_stride, LevelGeom g, u32* __rest
     }
 }
 
+// Staged block of eval_pts_kernel: limbs x in [-PTS_LO, roundup(estride, CH) + 4)
+// (the bottom-up pass reads x in [l0 - 2, l0 + 4) for every lane's l0 below
+// roundup(estride, CH); the sign scan x >= -2; shifts j i < 64 bits reach one
+// limb further down).
+constexpr int PTS_LO = 4;
+__host__ __device__ inline int pts_block_words(const LevelGeom& g) {
+    return PTS_LO + (g.estride + CH - 1) / CH * CH + 4;
+}
+
 // Short rows: one warp per row, every point of the row, the row staged in
 // shared memory (padded layout), several rows per block, no block barriers.
 // Warp per row for small B (B <= 8, every shift j i < 64 bits): the same staging
@@ -239,8 +248,9 @@ eval_pts_kernel(const u32* __restrict__ in, long in_stride, LevelGeom g, u32* __
     u32* rs = rows_sm + (long)warp * rowlen;
     const u32* row = in + k * in_stride;
     const int npts = 2 * BB - 1;
-    const int W = ((N - 1) * N >> 5) + 1;
-    const int bw = g.b + W;
+    // block i is staged as limbs x in [-PTS_LO, bw - PTS_LO), zeros outside [0, b),
+    // wide enough for every read below, so reads need no bounds checks
+    const int bw = pts_block_words(g);
     // all blocks' limbs of a round are loaded before any is stored, so the global
     // loads of a row are in flight together
     for (int r0 = 0; r0 < bw; r0 += 128) {
@@ -249,8 +259,8 @@ eval_pts_kernel(const u32* __restrict__ in, long in_stride, LevelGeom g, u32* __
         for (int i = 0; i < BB; ++i)
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                const int xo = r0 + lane + 32 * u, xi = xo - W, gi = i * g.b + xi;
-                v[i][u] = (xo < bw && xi >= 0 && gi < g.s) ? __ldg(row + gi) : 0u;
+                const int xo = r0 + lane + 32 * u, xi = xo - PTS_LO, gi = i * g.b + xi;
+                v[i][u] = (xo < bw && xi >= 0 && xi < g.b && gi < g.s) ? __ldg(row + gi) : 0u;
             }
 #pragma unroll
         for (int i = 0; i < BB; ++i)
@@ -261,8 +271,8 @@ eval_pts_kernel(const u32* __restrict__ in, long in_stride, LevelGeom g, u32* __
             }
     }
     __syncwarp();
-    auto U = [&](int i, int x) -> u32 {  // limb x of block i (zero outside [0, b))
-        return (x >= 0 && x < g.b) ? rs[pad32(i * bw + W + x)] : 0u;
+    auto U = [&](int i, int x) -> u32 {  // limb x of block i, -PTS_LO <= x < bw - PTS_LO
+        return rs[pad32(i * bw + PTS_LO + x)];
     };
     u32* orow0 = out + (k * npts) * (long)g.estride;
     for (int pos = 4 * lane; pos < g.estride; pos += CH) {
@@ -468,8 +478,9 @@ cudaError_t launch_eval(const u32* in, long in_stride, const LevelGeom& g, u32* 
     {
         const int W = ((g.n - 1) * g.n >> 5) + 1;
         const int staged = g.B * (g.b + W);
-        const int rowlen = pad32(staged) + 4;
+        int rowlen = pad32(staged) + 4;
         if (P >= 1024 && rowlen * 4 <= 12 * 1024) {
+            if (g.B <= 8) rowlen = pad32(g.B * pts_block_words(g)) + 4;
             static std::once_flag attr_once;
             std::call_once(attr_once, [] {
                 cudaFuncSetAttribute(eval_warp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
