@@ -1187,7 +1187,11 @@ interp_stream_kernel(InterpArgs a, DivTable dt, FinTable ft, long P) {
 
     // ---- pass A: even-odd combine and Newton loop 1 ----
     const int grow = (n * (n - 1) + 31) / 32 + 1;  // limbs of the deferred scale factors
-    const int stepsA = (Y + 2 * n + 2 + grow + C - 1) / C;
+    // every combine output and Newton coefficient fits in 2e limbs, so the windows
+    // stop once positions 2e + 2 and up (all zero) are reached; the tail of the
+    // work rows they would have written is zeroed after the pass
+    const int ext = 2 * g.e + 2 < Y ? 2 * g.e + 2 : Y;
+    const int stepsA = (ext + 2 * n + 2 + grow + C - 1) / C;
     for (int step = 0; step < stepsA; ++step) {
         const int base = C * step;  // absolute limb of an offset-0 window
         __syncwarp();
@@ -1319,6 +1323,12 @@ interp_stream_kernel(InterpArgs a, DivTable dt, FinTable ft, long P) {
             st_window<KL>(Wrow(1, kk), base - 2 * kk - 2, Y, v[1]);
         }
     }
+    // positions the windows did not reach (all at or above 2e + 2: zero)
+    for (int z = C * stepsA - 2 * n - 2 + lane; z < Y; z += 32)
+        for (int m = 0; m <= n; ++m) {
+            Wrow(0, m)[z] = 0u;
+            if (m >= 1) Wrow(1, m)[z] = 0u;
+        }
     __syncwarp();
     for (int i = lane; i < L.st1; i += 32) st1[i] = 0;
     __syncwarp();
@@ -1588,7 +1598,9 @@ interp_split_kernel(InterpArgs a, DivTable dt, FinTable ft, long P) {
 
         // ---- pass A: even-odd combine and Newton loop 1 ----
         const int grow = (n * (n - 1) + 31) / 32 + 1;  // limbs of the deferred scale factors
-        const int stepsA = (Y + 2 * n + 2 + grow + C - 1) / C;
+        // windows up to the values' real length 2e + 2, as in the one-warp kernel
+        const int ext = 2 * g.e + 2 < Y ? 2 * g.e + 2 : Y;
+        const int stepsA = (ext + 2 * n + 2 + grow + C - 1) / C;
         for (int step = 0; step < stepsA; ++step) {
             const int base = C * step;
             __syncwarp();
@@ -1736,6 +1748,9 @@ interp_split_kernel(InterpArgs a, DivTable dt, FinTable ft, long P) {
                 st_window_any<KL>(Wrow(p, kk), base - kk - 1, Y, v);
             }
         }
+        // positions the windows did not reach (all at or above 2e + 2: zero)
+        for (int z = C * stepsA - 2 * n - 2 + lane; z < Y; z += 32)
+            for (int m = p == 0 ? 0 : 1; m <= n; ++m) Wrow(p, m)[z] = 0u;
         __syncwarp();
         for (int i = lane; i < L.st1 + L.stb; i += 32) st1[i] = 0;
         __syncwarp();
