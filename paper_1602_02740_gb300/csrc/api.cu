@@ -254,21 +254,23 @@ tc_status run_uniform(const BatchLayout& L, char* base, size_t count, size_t s, 
         uint8_t* sU = reinterpret_cast<uint8_t*>(base + L.sgnU[l]);
         const double eval_bytes = 4.0 * L.P[l] * (g.s + (2.0 * g.B - 1) * g.estride) +
                                   (2.0 * g.B - 1) * L.P[l];
-        pt.begin(0, l, eval_bytes, 0);
         void* evw = base + L.evwork[l];
-        CK(launch_eval(inU, strU, g, eU, sU, L.P[l], evw, st));
-        pt.end();
-        inU = eU;
-        strU = g.estride;
-        if (!square) {
+        if (!square) {  // both operands (one launch for few rows)
             u32* eV = reinterpret_cast<u32*>(base + L.evalV[l]);
             uint8_t* sV = reinterpret_cast<uint8_t*>(base + L.sgnV[l]);
-            pt.begin(0, l, eval_bytes, 0);
-            CK(launch_eval(inV, strV, g, eV, sV, L.P[l], evw, st));
+            pt.begin(0, l, 2 * eval_bytes, 0);
+            CK(launch_eval2(inU, strU, eU, sU, inV, strV, eV, sV, g, L.P[l], evw, st));
             pt.end();
+            inU = eU;
+            strU = g.estride;
             inV = eV;
             strV = g.estride;
         } else {
+            pt.begin(0, l, eval_bytes, 0);
+            CK(launch_eval(inU, strU, g, eU, sU, L.P[l], evw, st));
+            pt.end();
+            inU = eU;
+            strU = g.estride;
             inV = inU;
             strV = strU;
         }

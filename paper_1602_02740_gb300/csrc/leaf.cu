@@ -114,38 +114,63 @@ leaf_kernel(const u32* __restrict__ A, long lda, const u32* __restrict__ Bm, lon
     }
     __syncthreads();
 
+    // Reduction, chunk-parallel: every warp takes (product, 128-column chunk) items,
+    // sums the row blocks' columns and normalises the chunk with carry-in 0 into the
+    // product's staging rows (dead after the tile pass; they hold 2s + 2H + 3 words);
+    // then one lane per product adds each chunk's carry out into the next chunk (it
+    // rarely ripples past a limb or two), and the block copies the limbs out.
     const int warp = tid >> 5, nwarps = nt >> 5, lane = tid & 31;
     const int out_len = 2 * g.s;
-    for (int k = warp; k < np; k += nwarps) {
+    const int nch = (out_len + CH - 1) / CH;
+    for (int item = warp; item < np * nch; item += nwarps) {
+        const int k = item / nch, ch = item - k * nch;
         const u32* part = sm + k * g.words + g.sa_len + g.sb_len;
-        u32* out = OUT + (p0 + k) * ldo;
-        const bool aligned = ((reinterpret_cast<uintptr_t>(out) & 15u) == 0);
-        UnsignedNorm st{0, 0};
-        for (int base = 0; base < out_len; base += CH) {
-            u64 cols[4];
+        u32* dig = sm + k * g.words;          // 2s digits, then the chunks' carries
+        u64 cols[4];
 #pragma unroll
-            for (int jj = 0; jj < 4; ++jj) {
-                const int c = base + 4 * lane + jj;
-                u64 S = 0;
-                for (int r = 0; r < g.RB; ++r) {
-                    const int x = c - r * g.H;
-                    if (x >= 0 && x < g.NW) S += part[(0 * g.RB + r) * g.NW + x];
-                    if (x - 1 >= 0 && x - 1 < g.NW) S += part[(1 * g.RB + r) * g.NW + x - 1];
-                    if (x - 2 >= 0 && x - 2 < g.NW) S += part[(2 * g.RB + r) * g.NW + x - 2];
-                }
-                cols[jj] = S;
+        for (int jj = 0; jj < 4; ++jj) {
+            const int c = ch * CH + 4 * lane + jj;
+            u64 S = 0;
+            for (int r = 0; r < g.RB; ++r) {
+                const int x = c - r * g.H;
+                if (x >= 0 && x < g.NW) S += part[(0 * g.RB + r) * g.NW + x];
+                if (x - 1 >= 0 && x - 1 < g.NW) S += part[(1 * g.RB + r) * g.NW + x - 1];
+                if (x - 2 >= 0 && x - 2 < g.NW) S += part[(2 * g.RB + r) * g.NW + x - 2];
             }
-            u32 d[4];
-            warp_norm_unsigned(cols, st, d);
-            const int pos = base + 4 * lane;
-            if (aligned && pos + 4 <= out_len) {
-                st4(out + pos, d);
-            } else {
+            cols[jj] = c < out_len ? S : 0;
+        }
+        UnsignedNorm st{0, 0};
+        u32 d[4];
+        warp_norm_unsigned(cols, st, d);
+        const int pos = ch * CH + 4 * lane;
 #pragma unroll
-                for (int jj = 0; jj < 4; ++jj)
-                    if (pos + jj < out_len) out[pos + jj] = d[jj];
+        for (int jj = 0; jj < 4; ++jj)
+            if (pos + jj < out_len) dig[pos + jj] = d[jj];
+        if (lane == 0) {  // carry out of the chunk: the last column's high part plus the carry bit
+            const u64 E = st.col_carry + st.carry;
+            dig[out_len + 2 * ch] = (u32)E;
+            dig[out_len + 2 * ch + 1] = (u32)(E >> 32);
+        }
+    }
+    __syncthreads();
+    for (int k = tid >> 5; k < np && lane == 0; k += nwarps) {
+        u32* dig = sm + k * g.words;
+        u64 E = 0;
+        for (int ch = 0; ch + 1 < nch; ++ch) {
+            E += (u64)dig[out_len + 2 * ch] | ((u64)dig[out_len + 2 * ch + 1] << 32);
+            for (int i = (ch + 1) * CH; E != 0 && i < out_len; ++i) {
+                if (i == (ch + 2) * CH) break;  // ran off this chunk: joins the next carry
+                const u64 v = (u64)dig[i] + E;
+                dig[i] = (u32)v;
+                E = v >> 32;
             }
         }
+    }
+    __syncthreads();
+    for (int k = 0; k < np; ++k) {
+        const u32* dig = sm + k * g.words;
+        u32* out = OUT + (p0 + k) * ldo;
+        for (int i = tid; i < out_len; i += nt) out[i] = dig[i];
     }
 }
 

@@ -44,6 +44,10 @@ cudaError_t launch_schoolbook_big(const uint32_t* A, long lda, const uint32_t* B
                                   cudaStream_t st);
 
 // `work`: wide_eval_work_bytes(g, P) bytes when use_wide_eval(g, P), else unused.
+// Both operands of P products (rows in / in2); one launch when P is small.
+cudaError_t launch_eval2(const uint32_t* in, long in_stride, uint32_t* out, uint8_t* sgn,
+                         const uint32_t* in2, long in2_stride, uint32_t* out2, uint8_t* sgn2,
+                         const LevelGeom& g, long P, void* work, cudaStream_t st);
 cudaError_t launch_eval(const uint32_t* in, long in_stride, const LevelGeom& g,
                         uint32_t* out, uint8_t* sgn, long P, void* work, cudaStream_t st);
 bool use_wide_eval(const LevelGeom& g, long P);

@@ -98,13 +98,23 @@ __device__ __forceinline__ void eval_finish(const u64 e[4], const u64 o[4], int 
 // 4t + c conflict-free.
 __host__ __device__ __forceinline__ int pad32(int x) { return x + (x >> 5); }
 
+// Blocks P .. 2P - 1 (when in2 is given) evaluate the second operand's rows into
+// out2 / sgn2, so both operands of few products take one launch.
 template <int MAXT, int MINB>
 __global__ void __launch_bounds__(MAXT, MINB)
 eval_kernel(const u32* __restrict__ in, long in_stride, LevelGeom g, u32* __restrict__ out,
-            uint8_t* __restrict__ sgn, long P) {
+            uint8_t* __restrict__ sgn, long P, const u32* __restrict__ in2, long in2_stride,
+            u32* __restrict__ out2, uint8_t* __restrict__ sgn2) {
     extern __shared__ __align__(16) u32 win[];  // [2][B][pad32(CH + W) + 1]
-    const long k = blockIdx.x;
-    if (k >= P) return;
+    long k = blockIdx.x;
+    if (k >= P) {
+        if (!in2 || k >= 2 * P) return;
+        k -= P;
+        in = in2;
+        in_stride = in2_stride;
+        out = out2;
+        sgn = sgn2;
+    }
     const u32* row = in + k * in_stride;
     const int npts = 2 * g.B - 1;
     u32* orow0 = out + (k * npts) * (long)g.estride;
@@ -470,6 +480,31 @@ eval_warp_kernel(const u32* __restrict__ in, long in_stride, LevelGeom g, u32* _
     }
 }
 
+cudaError_t launch_eval2(const u32* in, long in_stride, u32* out, uint8_t* sgn, const u32* in2,
+                         long in2_stride, u32* out2, uint8_t* sgn2, const LevelGeom& g, long P,
+                         void* work, cudaStream_t st) {
+    if (P <= 0) return cudaSuccess;
+    if (!(use_wide_eval(g, P) && work) && P < 1024) {
+        // few rows: the block-per-row kernel for both operands in one launch
+        const int warps = g.n < 1 ? 1 : g.n;
+        const int W = ((g.n - 1) * g.n >> 5) + 1;
+        const size_t smem = (size_t)2 * g.B * ((CH + W) + ((CH + W) >> 5) + 1) * 4;
+        if (warps * 32 <= 384) {
+            note_kernel("eval_kernel<384,3>");
+            eval_kernel<384, 3><<<(unsigned)(2 * P), warps * 32, smem, st>>>(in, in_stride, g, out, sgn, P,
+                                                                          in2, in2_stride, out2, sgn2);
+        } else {
+            note_kernel("eval_kernel<1024,1>");
+            eval_kernel<1024, 1><<<(unsigned)(2 * P), warps * 32, smem, st>>>(in, in_stride, g, out, sgn, P,
+                                                                           in2, in2_stride, out2, sgn2);
+        }
+        return cudaGetLastError();
+    }
+    cudaError_t e = launch_eval(in, in_stride, g, out, sgn, P, work, st);
+    if (e == cudaSuccess) e = launch_eval(in2, in2_stride, g, out2, sgn2, P, work, st);
+    return e;
+}
+
 cudaError_t launch_eval(const u32* in, long in_stride, const LevelGeom& g, u32* out,
                         uint8_t* sgn, long P, void* work, cudaStream_t st) {
     if (P <= 0) return cudaSuccess;
@@ -511,10 +546,12 @@ cudaError_t launch_eval(const u32* in, long in_stride, const LevelGeom& g, u32* 
     const size_t smem = (size_t)2 * g.B * ((CH + W) + ((CH + W) >> 5) + 1) * 4;  // two chunk buffers
     if (warps * 32 <= 384) {  // up to B = 13: three blocks per SM (at most 56 registers)
         note_kernel("eval_kernel<384,3>");
-        eval_kernel<384, 3><<<(unsigned)P, warps * 32, smem, st>>>(in, in_stride, g, out, sgn, P);
+        eval_kernel<384, 3><<<(unsigned)P, warps * 32, smem, st>>>(in, in_stride, g, out, sgn, P,
+                                                                    nullptr, 0, nullptr, nullptr);
     } else {
         note_kernel("eval_kernel<1024,1>");
-        eval_kernel<1024, 1><<<(unsigned)P, warps * 32, smem, st>>>(in, in_stride, g, out, sgn, P);
+        eval_kernel<1024, 1><<<(unsigned)P, warps * 32, smem, st>>>(in, in_stride, g, out, sgn, P,
+                                                                     nullptr, 0, nullptr, nullptr);
     }
     return cudaGetLastError();
 }
@@ -2233,7 +2270,9 @@ cudaError_t launch_interp(const LevelGeom& g, const u32* y, const uint8_t* su, c
         cudaFuncSetAttribute(interp_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
         cudaFuncSetAttribute(interp_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
     });
-    if (g.K == 8) {
+    // 8 limbs per lane whenever the values are whole 256-limb windows: half the
+    // windows per chain, and a lone product's interpolation is a chain of windows
+    if (g.K == 8 || g.Y % 256 == 0) {
         note_kernel("interp_kernel<8>");
         interp_kernel<8><<<(unsigned)P, warps * 32, smem, st>>>(a, dt8, P);
     } else {
