@@ -177,8 +177,8 @@ __device__ __forceinline__ void warp_norm_unsigned(const u64 cols[4], UnsignedNo
     for (int j = 1; j < 4; ++j) y[j] = (u64)d[j] + c[j - 1];
     // the lane's digits with carry-in 0 (y < 2^33 - 1, so every carry is 0 or 1);
     // then the carry out of the lane below, passed on only by an all-ones lane
-    // (a lane that carried out itself is at most 2^128 - 2 after it), one lane
-    // per round under a vote, as in warp_add_seg
+    // (a lane that carried out itself is at most 2^128 - 2 after it), whose
+    // chains a lookahead resolves when a vote finds any, as in warp_add_seg
     u32 x = 0;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -188,15 +188,16 @@ __device__ __forceinline__ void warp_norm_unsigned(const u64 cols[4], UnsignedNo
     }
     u32 cin = __shfl_up_sync(FULL, x, 1);
     if (lane == 0) cin = st.carry;
-    u32 o = inc4(out, cin);
-    u32 total = x | o;
-    while (__any_sync(FULL, o)) {
-        u32 t = __shfl_up_sync(FULL, o, 1);
-        if (lane == 0) t = 0;
-        o = inc4(out, t);
-        total |= o;
+    const u32 o = inc4(out, cin);
+    u32 cw = __shfl_sync(FULL, x | o, 31);
+    if (__any_sync(FULL, o)) {
+        u32 cout;
+        const bool ones = (out[0] & out[1] & out[2] & out[3]) == FULL;
+        const u32 e = warp_carry_scan(o != 0u, ones, 0u, &cout);
+        inc4(out, e);
+        cw |= cout;
     }
-    st.carry = __shfl_sync(FULL, total, 31);
+    st.carry = cw;
     st.col_carry = __shfl_sync(FULL, c[3], 31);
 }
 
@@ -383,10 +384,10 @@ __device__ __forceinline__ u32 dec_seg_out(u32 r[KL], u32 c) {
 // Warp-wide add of two chunks of 32 KL limbs.  Each lane adds its KL limbs with
 // carry-in 0 and then adds the carry out of the lane below (lane 0: the chunk's
 // carry-in).  That is the whole carry unless a lane's sum was all ones and
-// received a carry, which passes it on; such lanes (probability 2^-32KL on
-// uniform data, but common in structured values) are resolved one lane per
-// round until none is left, at most 31 rounds.  A lane gives out at most one
-// carry in total: one that produced a carry itself is not all ones after its
+// received a carry, which passes it on; when a vote finds such lanes (never on
+// uniform data, common in structured values such as all-ones operands) one
+// ballot lookahead finishes every chain.  A lane gives out at most one carry
+// in total: one that produced a carry itself is not all ones after its
 // carry-in.
 template <int KL>
 __device__ __forceinline__ void warp_add_seg(const u32 a[KL], const u32 b[KL], u32& carry, u32 r[KL]) {
@@ -394,15 +395,17 @@ __device__ __forceinline__ void warp_add_seg(const u32 a[KL], const u32 b[KL], u
     const u32 g = add_seg<KL>(a, b, 0u, r);
     u32 cin = __shfl_up_sync(FULL, g, 1);
     if (lane == 0) cin = carry;
-    u32 o = inc_seg_out<KL>(r, cin);
-    u32 out = g | o;
-    while (__any_sync(FULL, o)) {
-        u32 x = __shfl_up_sync(FULL, o, 1);
-        if (lane == 0) x = 0;
-        o = inc_seg_out<KL>(r, x);
-        out |= o;
+    const u32 o = inc_seg_out<KL>(r, cin);
+    u32 c = __shfl_sync(FULL, g | o, 31);
+    if (__any_sync(FULL, o)) {
+        // the rest of the chain in one lookahead: lanes that passed a carry on
+        // generate, lanes now all ones propagate; each lane adds its extra carry
+        u32 cout;
+        const u32 x = warp_carry_scan(o != 0u, ones_seg<KL>(r), 0u, &cout);
+        inc_seg<KL>(r, x);
+        c |= cout;
     }
-    carry = __shfl_sync(FULL, out, 31);
+    carry = c;
 }
 
 // The same for r = a - b with borrows (a propagating lane: difference 0).
@@ -412,15 +415,15 @@ __device__ __forceinline__ void warp_sub_seg(const u32 a[KL], const u32 b[KL], u
     const u32 g = sub_seg<KL>(a, b, 0u, r);
     u32 bin = __shfl_up_sync(FULL, g, 1);
     if (lane == 0) bin = borrow;
-    u32 o = dec_seg_out<KL>(r, bin);
-    u32 out = g | o;
-    while (__any_sync(FULL, o)) {
-        u32 x = __shfl_up_sync(FULL, o, 1);
-        if (lane == 0) x = 0;
-        o = dec_seg_out<KL>(r, x);
-        out |= o;
+    const u32 o = dec_seg_out<KL>(r, bin);
+    u32 c = __shfl_sync(FULL, g | o, 31);
+    if (__any_sync(FULL, o)) {
+        u32 bout;
+        const u32 x = warp_carry_scan(o != 0u, zero_seg<KL>(r), 0u, &bout);
+        dec_seg<KL>(r, x);
+        c |= bout;
     }
-    borrow = __shfl_sync(FULL, out, 31);
+    borrow = c;
 }
 
 // The same add and subtract with every lane's carry resolved by the lookahead
