@@ -751,7 +751,7 @@ def main():
     hA = torch.from_numpy(A.view(np.int32)).pin_memory()
     hB = torch.from_numpy(B.view(np.int32)).pin_memory()
     hO = torch.empty((P, 2 * L), dtype=torch.int32).pin_memory()
-    e2e_steps = max(3, min(args.steps, 10))
+    e2e_steps = max(3, min(args.steps, 20))
     # pipelined entry point: each step copies its inputs in and its products out,
     # two steps in flight (copies overlap the kernels of the neighbouring step)
     pipe = tc.tc_pipe_create(ctx, P, L, plan=used_plan)
