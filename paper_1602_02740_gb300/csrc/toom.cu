@@ -484,8 +484,11 @@ cudaError_t launch_eval2(const u32* in, long in_stride, u32* out, uint8_t* sgn, 
                          long in2_stride, u32* out2, uint8_t* sgn2, const LevelGeom& g, long P,
                          void* work, cudaStream_t st) {
     if (P <= 0) return cudaSuccess;
-    if (!(use_wide_eval(g, P) && work) && P < 1024) {
-        // few rows: the block-per-row kernel for both operands in one launch
+    const int Wh = ((g.n - 1) * g.n >> 5) + 1;
+    const bool warp_rows = P >= 1024 && (pad32(g.B * (g.b + Wh)) + 4) * 4 <= 12 * 1024;
+    if (!(use_wide_eval(g, P) && work) && !warp_rows) {
+        // the block-per-row kernel (few rows, or long ones): both operands in one
+        // launch, which also halves the partly filled last waves
         const int warps = g.n < 1 ? 1 : g.n;
         const int W = ((g.n - 1) * g.n >> 5) + 1;
         const size_t smem = (size_t)2 * g.B * ((CH + W) + ((CH + W) >> 5) + 1) * 4;
