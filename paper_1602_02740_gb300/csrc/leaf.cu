@@ -15,8 +15,10 @@
 // eight limbs of b (two 16-byte loads) feed 16 limb products.
 //
 // Reduction.  Tiles write their column accumulators to shared memory, one
-// window of columns per row block; a warp per product then sums the row
-// blocks per output limb and resolves carries with the warp scans.
+// window of columns per row block; then every warp takes 128-column chunks of
+// the products, sums the row blocks per output limb and normalises the chunk,
+// one lane per product adds each chunk's carry into the next, and the block
+// writes the limbs out.
 #include <mutex>
 
 #include "../../include/tc.h"
