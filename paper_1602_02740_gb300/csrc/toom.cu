@@ -277,18 +277,24 @@ eval_pts_kernel(const u32* __restrict__ in, long in_stride, LevelGeom g, u32* __
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int xo = r0 + lane + 32 * u;
-                if (xo < bw) rs[pad32(i * bw + xo)] = v[i][u];
+                if (xo < bw) rs[i * bw + xo] = v[i][u];
             }
     }
     __syncwarp();
+    // Unpadded: the scalar reads below are consecutive across lanes, and the
+    // bottom-up pass reads each lane's four limbs as one 16-byte vector
+    // (bw and PTS_LO are multiples of 4) and the two below from the lane below.
     auto U = [&](int i, int x) -> u32 {  // limb x of block i, -PTS_LO <= x < bw - PTS_LO
-        return rs[pad32(i * bw + PTS_LO + x)];
+        return rs[i * bw + PTS_LO + x];
+    };
+    auto U4 = [&](int i, int x, u32 v[4]) {  // limbs x .. x + 3 of block i, x a multiple of 4
+        const uint4 q = *reinterpret_cast<const uint4*>(rs + i * bw + PTS_LO + x);
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
     };
     u32* orow0 = out + (k * npts) * (long)g.estride;
     for (int pos = 4 * lane; pos < g.estride; pos += CH) {
         u32 v[4];
-#pragma unroll
-        for (int jj = 0; jj < 4; ++jj) v[jj] = (pos + jj < g.s) ? U(0, pos + jj) : 0u;
+        U4(0, pos, v);  // zero past b
         st4(orow0 + pos, v);
     }
     // ---- signs of E - O at every x = 2^j, top-down, loads shared ----
@@ -346,9 +352,12 @@ eval_pts_kernel(const u32* __restrict__ in, long in_stride, LevelGeom g, u32* __
         const int l0 = base + 4 * lane;
         u32 v[BB][6];  // limbs l0-2 .. l0+3 of each block
 #pragma unroll
-        for (int i = 0; i < BB; ++i)
-#pragma unroll
-            for (int q = 0; q < 6; ++q) v[i][q] = U(i, l0 - 2 + q);
+        for (int i = 0; i < BB; ++i) {
+            U4(i, l0, v[i] + 2);
+            const u32 b2 = __shfl_up_sync(FULL, v[i][4], 1), b3 = __shfl_up_sync(FULL, v[i][5], 1);
+            v[i][0] = lane == 0 ? U(i, l0 - 2) : b2;
+            v[i][1] = lane == 0 ? U(i, l0 - 1) : b3;
+        }
 #pragma unroll
         for (int j = 0; j < N; ++j) {
             u64 e[4] = {0, 0, 0, 0}, o[4] = {0, 0, 0, 0};
@@ -518,7 +527,7 @@ cudaError_t launch_eval(const u32* in, long in_stride, const LevelGeom& g, u32* 
         const int staged = g.B * (g.b + W);
         int rowlen = pad32(staged) + 4;
         if (P >= 1024 && rowlen * 4 <= 12 * 1024) {
-            if (g.B <= 8) rowlen = pad32(g.B * pts_block_words(g)) + 4;
+            if (g.B <= 8) rowlen = g.B * pts_block_words(g) + 4;  // unpadded, 16-byte rows
             static std::once_flag attr_once;
             std::call_once(attr_once, [] {
                 cudaFuncSetAttribute(eval_warp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
