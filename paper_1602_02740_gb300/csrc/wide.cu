@@ -198,17 +198,15 @@ __device__ u32 div_lookback(u64* st, int seg, u32 bo0, const WideDiv& D, int* er
     if (lane_id() == 0) {
         st_rel(st + seg, F_AGG | bo0);
         u32 acc = 0, mult = D.onem;
-        bool found = false;
         for (int j = seg - 1; j >= 0; --j) {
             const u64 v = wait_status(st + j, err);
             const u32 x = (u32)v;
             const u32 add = mont_mul(mult, x, D.d, D.ninv);
             const u32 s = acc + add;
             acc = s >= D.d ? s - D.d : s;
-            if ((v & F_MASK) == F_INCL) { found = true; break; }
+            if ((v & F_MASK) == F_INCL) break;
             mult = mont_mul(mult, D.segm, D.d, D.ninv);
         }
-        (void)found;
         bin = acc;  // no inclusive predecessor: the chain's borrow-in is 0
         const u32 s = bo0 + mont_mul(D.segm, bin, D.d, D.ninv);
         st_rel(st + seg, F_INCL | (s >= D.d ? s - D.d : s));
