@@ -262,6 +262,15 @@ def cpu_baselines(limbs: int, plan, seconds: float = 6.0):
     }
 
 
+def headline_config(P, L, plan):
+    """The workload description both arms print (the reference arm times a
+    bounded sample of it, stated in its cpu_baseline)."""
+    return {"workload": f"batch of {P} balanced {L * 32}-bit products per GPU, "
+                        "uniform random limbs (B sweep at 2^20 bits)",
+            "limbs": L, "batch_per_gpu": P, "plan": plan,
+            "l2": f"operands ({2 * P * L * 4 / 1e6:.0f} MB) exceed the 129 MB L2; no flush"}
+
+
 def run_reference(args, rank, world):
     """The reference arm: the oracle's C Toom-Cook (the same method, plain C,
     no GPU) on the host cores, whole products per thread, on the bench's
@@ -291,8 +300,7 @@ def run_reference(args, rank, world):
             "value": value, "unit": "mults/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": count / value * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": f"balanced {limbs * 32}-bit products, uniform limbs",
-                       "limbs": limbs, "plan": plan},
+            "config": headline_config(args.batch, limbs, plan),
             "cpu_baseline": cpu,
             "e2e": {"value": value, "unit": "mults/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -871,10 +879,7 @@ def main():
             "ns_per_product": ms_step * 1e6 / P,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
             "data": "synthetic",
-            "config": {"workload": f"batch of {P} balanced {L * 32}-bit products per GPU, "
-                                   "uniform random limbs (B sweep at 2^20 bits)",
-                       "limbs": L, "batch_per_gpu": P, "plan": used_plan,
-                       "l2": f"operands ({2 * P * L * 4 / 1e6:.0f} MB) exceed the 129 MB L2; no flush"},
+            "config": headline_config(P, L, used_plan),
             "verified": verified,
             "roofline": roof, "rooflines": roofs, "int_ceiling": ceiling,
             "phases": [{"kind": p["kind"], "level": p["level"], "kernel": p["kernel"],
